@@ -1,0 +1,178 @@
+/*
+ * sw.h -- C ABI of libsw: Swendsen-Wang dynamics of the 2D Ising model on a
+ * periodic square lattice, run on one GB300 (sm_103a).
+ *
+ * A sweep is the three computing steps of the paper's §2 (Swendsen-Wang
+ * Algorithm): bond formation (§2.1), cluster formation (§2.3) and assignment
+ * of new spins (§2.4), followed by the energy and magnetisation measurement
+ * that closes §2 (H = -sum_<ij> s_i s_j, M = sum_i s_i). The erasure steps
+ * (§2.2, §2.5) need no code: new spins overwrite the old ones and bonds are
+ * transient.
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions (the paper fixes none of these; every result below is integer
+ * and fully determined by them, so two implementations agree bit for bit)
+ * ---------------------------------------------------------------------------
+ *  C1  Lattice L x L, periodic. site = y*L + x. The east neighbour of (y,x) is
+ *      (y,(x+1)%L), the south neighbour ((y+1)%L,x). Each site owns its east
+ *      and south edge (§2.1 and Fig. 2: a site checks the neighbours to its
+ *      east and south), so there are 2N edges, N = L*L. For L = 2 the two
+ *      edges between a pair of sites are distinct edges.
+ *  C2  Bond probability p = 1 - exp(-2*beta*J), J = 1. (§2.1 prints
+ *      1 - exp(-1/k_B T); with H = -sum s_i s_j from §2 the Swendsen-Wang rule
+ *      is 1 - exp(-2 beta), and only that reading puts the transition the
+ *      paper reports in §4 (k_B T ~ 2.25) at the Onsager point 2.269.)
+ *  C3  Threshold, computed once on the host in binary64:
+ *        thr = (uint32) min(floor(ldexp(-expm1(-2*beta), 32)), 0xFFFFFFFF).
+ *      A like-spin pair bonds iff its Philox word u satisfies u < thr
+ *      (strict). beta must be finite and >= 0. The beta used is the literal
+ *      value passed in.
+ *  C4  Generator: Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw,
+ *      "Parallel random numbers: as easy as 1, 2, 3", SC'11). Key
+ *      (k0,k1) = (seed & 0xffffffff, seed >> 32); counter (c0,c1,c2,c3);
+ *      output words x0..x3.
+ *  C5  Bond draws of sweep t: counter (site>>1, t, 0, 0); site i takes word
+ *      x[2*(i&1) + dir], dir 0 = east, 1 = south. One Philox block serves two
+ *      consecutive sites and both directions.
+ *  C6  Cluster flip of sweep t: counter (root, t, 1, 0), word x0, where root
+ *      is the cluster's canonical label (C9). The cluster flips iff
+ *      x0 >> 31 == 1; then every site of it takes s <- -s. (The paper's
+ *      §2.4 assigns each cluster a fresh random spin; with monochrome
+ *      clusters both rules give the same distribution.)
+ *  C7  Hot start: counter (site, 0, 2, 0), word x0; s = (x0>>31) ? -1 : +1.
+ *      Cold start: every spin +1.
+ *  C8  Sweep counter t starts at 0 at creation and grows by one per sweep,
+ *      across calls: sw_sweep(h,a); sw_sweep(h,b) == sw_sweep(h,a+b).
+ *  C9  Labels: label[i] = the smallest site index in the bond-connected
+ *      cluster of i (the "lowest value label" of §2.3). The cluster's root
+ *      is that site. int32, so L*L < 2^31 (L <= 46340); L >= 2.
+ *  C10 Observables after each sweep, int64: E = -sum_i s_i (s_E(i) + s_S(i))
+ *      over the 2N edges, M = sum_i s_i (§2 divides M by N; the caller
+ *      divides).
+ *  C11 Cluster statistics (optional, per sweep): n_clusters, sum_C |C|^2,
+ *      and 32 log2 bins, bin k = number of clusters with 2^k <= |C| < 2^(k+1).
+ *
+ * ---------------------------------------------------------------------------
+ * General rules
+ * ---------------------------------------------------------------------------
+ *  - Every call returns SW_OK (0) or a negative status below; after a
+ *    failure sw_last_error() gives a message (thread-local).
+ *  - The library owns all device memory of a handle. Host buffers passed in
+ *    belong to the caller and are only read or written during the call.
+ *  - A device pointer passed with *_is_device = 1 must be device memory of
+ *    the handle's device; the call orders itself on the handle's stream.
+ *  - Work runs asynchronously on the handle's stream; calls that return data
+ *    to the host (sw_observables, sw_histograms, host-buffer forms of
+ *    sw_labels/sw_spins/sw_bonds) synchronise that stream and check the
+ *    device error flag (SW_EDEVICE / SW_ETIMEOUT).
+ *  - There is no CPU fallback: without a usable GPU, sw_create returns
+ *    SW_ECUDA.
+ */
+#ifndef SW_H
+#define SW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SW_OK        0
+#define SW_EINVAL   (-1)  /* bad argument: L<2, L*L >= 2^31, beta not finite or < 0, n < 0, range */
+#define SW_ENOMEM   (-2)  /* device or host allocation failed */
+#define SW_ECUDA    (-3)  /* a CUDA runtime call failed (includes: no GPU) */
+#define SW_EDEVICE  (-4)  /* a kernel raised the device error flag (an internal bound was exceeded) */
+#define SW_ETIMEOUT (-5)  /* a capped device-side wait or retry loop gave up */
+
+#define SW_INIT_HOT  0
+#define SW_INIT_COLD 1
+
+/* int64 words per sweep written by sw_histograms: n_clusters, sum |C|^2, 32 bins (C11). */
+#define SW_HIST_WORDS 34
+
+typedef struct sw_lattice sw_lattice;
+
+/* Bond threshold of C3 for inverse temperature beta (§2.1 bond probability,
+ * read as p = 1 - exp(-2 beta)). Returns 0 for beta = 0 and 0xFFFFFFFF once p
+ * rounds to 1. For beta < 0, NaN or inf it returns 0 and sets the last error;
+ * sw_create rejects such beta with SW_EINVAL. Pure host function. */
+uint32_t sw_threshold(double beta);
+
+/* Create a lattice of side L at inverse temperature beta.
+ *  L      : 2 <= L <= 46340.
+ *  beta   : finite, >= 0.
+ *  seed   : Philox key (C4).
+ *  init   : SW_INIT_HOT (C7) or SW_INIT_COLD (all +1).
+ *  stream : a cudaStream_t of the current device, or NULL for a stream the
+ *           library creates and owns. All work of the handle runs on it.
+ *  out    : receives the handle. The handle owns its device memory (int8
+ *           spins [L][L] row-major, tile records, per-sweep trace) until
+ *           sw_destroy.
+ * The sweep counter starts at 0 (C8). The initial state is not part of the
+ * trace. Errors: SW_EINVAL, SW_ENOMEM, SW_ECUDA. */
+int sw_create(int32_t L, double beta, uint64_t seed, int32_t init, void* stream,
+              sw_lattice** out);
+
+/* Release every resource of h (synchronises its stream first). NULL is a no-op. */
+int sw_destroy(sw_lattice* h);
+
+/* Run n >= 0 sweeps (§2: bonds §2.1, clusters §2.3, new spins §2.4, then
+ * the E/M measurement) asynchronously on the handle's stream; sweeps use
+ * counters t, t+1, ..., t+n-1 and the counter ends at t+n (C8). After each
+ * sweep E and M (C10), and the C11 statistics if enabled, are appended to
+ * the device-side trace. Errors: SW_EINVAL (n < 0), SW_ENOMEM (trace
+ * growth), SW_ECUDA. Device-side failures are reported by the next call that
+ * synchronises. */
+int sw_sweep(sw_lattice* h, int32_t n);
+
+/* Current sweep counter t (the counter the next sweep will use). */
+int sw_get_sweep(sw_lattice* h, uint32_t* t_out);
+
+/* Copy E and M (C10) of sweeps [first, first+count) to the host arrays
+ * E_host[count], M_host[count] (either may be NULL). Sweep indices are
+ * absolute counters; the trace holds the sweeps run since sw_create or the
+ * last sw_set_state, so first must be >= that start and first+count <= the
+ * current counter, else SW_EINVAL. Synchronises; checks the error flag. */
+int sw_observables(sw_lattice* h, int64_t first, int64_t count,
+                   int64_t* E_host, int64_t* M_host);
+
+/* Enable (1) or disable (0) the per-sweep C11 cluster statistics for the
+ * sweeps that follow. Sweeps run while disabled read back as zeros. */
+int sw_histogram(sw_lattice* h, int32_t enable);
+
+/* Copy the C11 statistics of sweeps [first, first+count) to
+ * out_host[count][SW_HIST_WORDS] (int64, row per sweep). Same range rules
+ * and synchronisation as sw_observables. */
+int sw_histograms(sw_lattice* h, int64_t first, int64_t count, int64_t* out_host);
+
+/* Canonical cluster labels (C9, §2.3) of the bond graph that the NEXT sweep
+ * (counter t) draws from the current spins; the state is not changed.
+ * out: int32 [L][L]; host memory if out_is_device == 0 (then the call
+ * synchronises), else device memory of the handle's device (asynchronous
+ * on the handle's stream). */
+int sw_labels(sw_lattice* h, int32_t* out, int32_t out_is_device);
+
+/* Current spins, int8 [L][L] row-major, values +1/-1. Host or device out as
+ * for sw_labels. */
+int sw_spins(sw_lattice* h, int8_t* out, int32_t out_is_device);
+
+/* Replace the state: spins int8 [L][L] (every value must be +1 or -1, else
+ * SW_EINVAL for host input; device input is checked on the device and
+ * reported as SW_EINVAL by the next synchronising call) and the sweep
+ * counter t. Clears the trace (its start becomes t). Used to resume a run
+ * from a checkpoint and for spot checks. */
+int sw_set_state(sw_lattice* h, const int8_t* spins, uint32_t t, int32_t in_is_device);
+
+/* Debug export of the bonds that the NEXT sweep (counter t) draws from the
+ * current spins (§2.1): out_host uint8 [L][L], bit0 = east bond,
+ * bit1 = south bond. Synchronises. The state is not changed. */
+int sw_bonds(sw_lattice* h, uint8_t* out_host);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SW_H */
