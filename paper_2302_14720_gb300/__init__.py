@@ -1,0 +1,223 @@
+"""Swendsen-Wang dynamics of the 2D Ising model on one GB300 (sm_103a).
+
+Thin ctypes binding of libsw (include/sw.h). Every function below has the
+name of the C entry point it marshals; it converts arguments and statuses
+and nothing else -- all sweep arithmetic runs in the library's CUDA kernels.
+There is no CPU fallback: importing the binding raises if libsw.so has not
+been built (``paper_2302_14720_gb300.build.build()``), and ``sw_create``
+fails without a GPU.
+
+Device buffers and streams may come from PyTorch: pass ``tensor.data_ptr()``
+with ``*_is_device=True`` and ``torch.cuda.current_stream().cuda_stream`` as
+the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB_PATH
+
+SW_OK = 0
+SW_EINVAL = -1
+SW_ENOMEM = -2
+SW_ECUDA = -3
+SW_EDEVICE = -4
+SW_ETIMEOUT = -5
+SW_INIT_HOT = 0
+SW_INIT_COLD = 1
+SW_HIST_WORDS = 34
+
+_STATUS_NAMES = {SW_EINVAL: "SW_EINVAL", SW_ENOMEM: "SW_ENOMEM", SW_ECUDA: "SW_ECUDA",
+                 SW_EDEVICE: "SW_EDEVICE", SW_ETIMEOUT: "SW_ETIMEOUT"}
+
+# Every symbol include/sw.h declares, with its ctypes signature.
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "sw_threshold": (ctypes.c_uint32, [ctypes.c_double]),
+    "sw_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32, _P,
+                                 ctypes.POINTER(_P)]),
+    "sw_destroy": (ctypes.c_int, [_P]),
+    "sw_sweep": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sw_get_sweep": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32)]),
+    "sw_observables": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "sw_histogram": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sw_histograms": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P]),
+    "sw_labels": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "sw_spins": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "sw_set_state": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_int32]),
+    "sw_bonds": (ctypes.c_int, [_P, _P]),
+    "sw_last_error": (ctypes.c_char_p, []),
+}
+
+
+class SWError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsw is not built ({LIB_PATH} missing); run paper_2302_14720_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+LIBRARY_PATH = LIB_PATH
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != SW_OK:
+        raise SWError(rc, where, _lib.sw_last_error().decode())
+
+
+def _host_ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ----------------------------------------------------------------- functions
+
+def sw_threshold(beta: float) -> int:
+    return int(_lib.sw_threshold(float(beta)))
+
+
+def sw_create(L: int, beta: float, seed: int, init: int = SW_INIT_HOT, stream: int | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.sw_create(int(L), float(beta), int(seed) & 0xFFFFFFFFFFFFFFFF, int(init),
+                          ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)), "sw_create")
+    return h.value
+
+
+def sw_destroy(h: int) -> None:
+    _check(_lib.sw_destroy(h), "sw_destroy")
+
+
+def sw_sweep(h: int, n: int) -> None:
+    _check(_lib.sw_sweep(h, int(n)), "sw_sweep")
+
+
+def sw_get_sweep(h: int) -> int:
+    t = ctypes.c_uint32()
+    _check(_lib.sw_get_sweep(h, ctypes.byref(t)), "sw_get_sweep")
+    return t.value
+
+
+def sw_observables(h: int, first: int, count: int):
+    E = np.zeros(max(count, 0), np.int64)
+    M = np.zeros(max(count, 0), np.int64)
+    _check(_lib.sw_observables(h, int(first), int(count), _host_ptr(E), _host_ptr(M)), "sw_observables")
+    return E, M
+
+
+def sw_histogram(h: int, enable: bool) -> None:
+    _check(_lib.sw_histogram(h, 1 if enable else 0), "sw_histogram")
+
+
+def sw_histograms(h: int, first: int, count: int) -> np.ndarray:
+    out = np.zeros((max(count, 0), SW_HIST_WORDS), np.int64)
+    _check(_lib.sw_histograms(h, int(first), int(count), _host_ptr(out)), "sw_histograms")
+    return out
+
+
+def sw_labels(h: int, L: int, out_device_ptr: int | None = None):
+    """Host int32 [L, L] labels, or write to a device pointer when given."""
+    if out_device_ptr is not None:
+        _check(_lib.sw_labels(h, ctypes.c_void_p(out_device_ptr), 1), "sw_labels")
+        return None
+    out = np.zeros((L, L), np.int32)
+    _check(_lib.sw_labels(h, _host_ptr(out), 0), "sw_labels")
+    return out
+
+
+def sw_spins(h: int, L: int, out_device_ptr: int | None = None):
+    if out_device_ptr is not None:
+        _check(_lib.sw_spins(h, ctypes.c_void_p(out_device_ptr), 1), "sw_spins")
+        return None
+    out = np.zeros((L, L), np.int8)
+    _check(_lib.sw_spins(h, _host_ptr(out), 0), "sw_spins")
+    return out
+
+
+def sw_set_state(h: int, spins, t: int, in_device_ptr: bool = False) -> None:
+    """spins: int8 numpy array (host) or an integer device pointer with in_device_ptr=True."""
+    if in_device_ptr:
+        _check(_lib.sw_set_state(h, ctypes.c_void_p(int(spins)), int(t) & 0xFFFFFFFF, 1), "sw_set_state")
+        return
+    s = np.ascontiguousarray(spins, dtype=np.int8)
+    _check(_lib.sw_set_state(h, _host_ptr(s), int(t) & 0xFFFFFFFF, 0), "sw_set_state")
+
+
+def sw_bonds(h: int, L: int) -> np.ndarray:
+    out = np.zeros((L, L), np.uint8)
+    _check(_lib.sw_bonds(h, _host_ptr(out)), "sw_bonds")
+    return out
+
+
+def sw_last_error() -> str:
+    return _lib.sw_last_error().decode()
+
+
+# ------------------------------------------------------------ convenience
+
+class Lattice:
+    """Owning wrapper of one sw_lattice handle."""
+
+    def __init__(self, L: int, beta: float, seed: int, init: int = SW_INIT_HOT, stream: int | None = None):
+        self.L = int(L)
+        self.beta = float(beta)
+        self.seed = int(seed)
+        self.h = sw_create(L, beta, seed, init, stream)
+
+    def sweep(self, n: int = 1) -> None:
+        sw_sweep(self.h, n)
+
+    @property
+    def t(self) -> int:
+        return sw_get_sweep(self.h)
+
+    def observables(self, first: int, count: int):
+        return sw_observables(self.h, first, count)
+
+    def histograms(self, first: int, count: int) -> np.ndarray:
+        return sw_histograms(self.h, first, count)
+
+    def histogram(self, enable: bool) -> None:
+        sw_histogram(self.h, enable)
+
+    def spins(self) -> np.ndarray:
+        return sw_spins(self.h, self.L)
+
+    def labels(self) -> np.ndarray:
+        return sw_labels(self.h, self.L)
+
+    def bonds(self) -> np.ndarray:
+        return sw_bonds(self.h, self.L)
+
+    def set_state(self, spins, t: int) -> None:
+        sw_set_state(self.h, spins, t)
+
+    def close(self) -> None:
+        if self.h:
+            sw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,382 @@
+// sw_api.cu -- the C ABI of libsw (include/sw.h): handles, device memory,
+// the per-sweep trace, argument checks and error reporting. All arithmetic
+// of a sweep runs in the kernels of sw_kernels.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+#include <string>
+
+#include "sw.h"
+#include "sw_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? SW_ENOMEM : SW_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SW_CUDA(call, what)                          \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+bool beta_ok(double beta) { return isfinite(beta) && beta >= 0.0; }
+
+uint32_t threshold_of(double beta) {
+  // C3: thr = floor(2^32 * (1 - exp(-2 beta))), capped at 2^32 - 1
+  const double p = -expm1(-2.0 * beta);
+  const double scaled = floor(ldexp(p, 32));
+  if (scaled >= 4294967295.0) return 0xffffffffu;
+  return (uint32_t)scaled;
+}
+
+int shape_for(int L) {
+  if (const char* env = getenv("SW_TILE_SHAPE")) {
+    const int v = atoi(env);
+    if (v >= 0 && v < sw::kNumShapes) return v;
+  }
+  return L <= 64 ? 2 : 0;
+}
+
+}  // namespace
+
+struct sw_lattice {
+  int L = 0;
+  double beta = 0.0;
+  uint64_t seed = 0;
+  uint32_t thr = 0;
+  int64_t t = 0;       // next sweep counter (absolute)
+  int64_t t_base = 0;  // first sweep held in the trace
+  int64_t cap = 0;     // trace capacity in sweeps
+  int shape = 0;
+  int device = 0;
+  bool hist_on = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  sw::Geometry g{};
+  sw::KeySchedule ks{};
+  sw::TileBuffers tb{};
+  int8_t* spins = nullptr;
+  uint32_t* csize = nullptr;
+  int64_t* em = nullptr;    // [cap][2]
+  int64_t* hist = nullptr;  // [cap][SW_HIST_WORDS]
+  int32_t* label_buf = nullptr;
+  uint8_t* bond_buf = nullptr;
+};
+
+namespace {
+
+void free_all(sw_lattice* h) {
+  void* ptrs[] = {h->spins, h->tb.tbits, h->tb.nodes, h->tb.bslot, h->tb.bbits, h->tb.nslots, h->tb.err,
+                  h->csize, h->em, h->hist, h->label_buf, h->bond_buf};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+sw::SweepArgs args_of(const sw_lattice* h) {
+  sw::SweepArgs a{};
+  a.g = h->g;
+  a.thr = h->thr;
+  a.t = (uint32_t)h->t;
+  a.ks = h->ks;
+  a.tb = h->tb;
+  a.spins_in = h->spins;
+  a.spins_out = h->spins;
+  return a;
+}
+
+int ensure_trace(sw_lattice* h, int64_t sweeps_needed) {
+  if (sweeps_needed <= h->cap) return SW_OK;
+  int64_t ncap = h->cap ? h->cap : 1024;
+  while (ncap < sweeps_needed) ncap *= 2;
+  int64_t *em = nullptr, *hist = nullptr;
+  cudaError_t e = cudaMalloc(&em, (size_t)ncap * 2 * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&hist, (size_t)ncap * SW_HIST_WORDS * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, (size_t)ncap * SW_HIST_WORDS * sizeof(int64_t), h->stream);
+  if (e == cudaSuccess && h->cap) {
+    e = cudaMemcpyAsync(em, h->em, (size_t)h->cap * 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hist, h->hist, (size_t)h->cap * SW_HIST_WORDS * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                          h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    if (em) cudaFree(em);
+    if (hist) cudaFree(hist);
+    return cuda_fail(e, "trace growth");
+  }
+  if (h->em) cudaFree(h->em);
+  if (h->hist) cudaFree(h->hist);
+  h->em = em;
+  h->hist = hist;
+  h->cap = ncap;
+  return SW_OK;
+}
+
+// Synchronise the handle's stream and turn the device error flag into a status.
+int sync_and_check(sw_lattice* h) {
+  SW_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+  int flag = 0;
+  SW_CUDA(cudaMemcpy(&flag, h->tb.err, sizeof(int), cudaMemcpyDeviceToHost), "error flag read");
+  switch (flag) {
+    case sw::kErrNone: return SW_OK;
+    case sw::kErrUnionCap: return fail(SW_ETIMEOUT, "device union-find retry loop reached its cap");
+    case sw::kErrBadSpin: return fail(SW_EINVAL, "sw_set_state: device spins contain values other than +1/-1");
+    case sw::kErrSlotOverflow: return fail(SW_EDEVICE, "device: tile border slots overflowed");
+    default: return fail(SW_EDEVICE, "device error flag %d", flag);
+  }
+}
+
+int range_ok(const sw_lattice* h, int64_t first, int64_t count) {
+  if (count < 0 || first < h->t_base || first + count > h->t)
+    return fail(SW_EINVAL, "sweeps [%lld, %lld) outside the trace [%lld, %lld)", (long long)first,
+                (long long)(first + count), (long long)h->t_base, (long long)h->t);
+  return SW_OK;
+}
+
+// Phases 1-2 for the current state and counter (bonds, tile clusters, merge).
+int run_clusters(sw_lattice* h, sw::SweepArgs& a) {
+  a.em = nullptr;
+  a.hist = nullptr;
+  a.csize = nullptr;
+  SW_CUDA(sw::launch_phase1(h->shape, a, h->stream), "phase 1 launch");
+  SW_CUDA(sw::launch_phase2(h->shape, a, h->stream), "phase 2 launch");
+  return SW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint32_t sw_threshold(double beta) {
+  if (!beta_ok(beta)) {
+    fail(SW_EINVAL, "beta must be finite and >= 0");
+    return 0u;
+  }
+  return threshold_of(beta);
+}
+
+const char* sw_last_error(void) { return g_last_error.c_str(); }
+
+int sw_create(int32_t L, double beta, uint64_t seed, int32_t init, void* stream, sw_lattice** out) {
+  if (!out) return fail(SW_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (L < 2 || (int64_t)L * L >= ((int64_t)1 << 31)) return fail(SW_EINVAL, "L=%d outside 2 <= L, L*L < 2^31", L);
+  if (!beta_ok(beta)) return fail(SW_EINVAL, "beta must be finite and >= 0");
+  if (init != SW_INIT_HOT && init != SW_INIT_COLD) return fail(SW_EINVAL, "init must be SW_INIT_HOT or SW_INIT_COLD");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(SW_ECUDA, "no CUDA device available (libsw has no CPU fallback)");
+  }
+  sw_lattice* h = new (std::nothrow) sw_lattice();
+  if (!h) return fail(SW_ENOMEM, "host allocation failed");
+  h->L = L;
+  h->beta = beta;
+  h->seed = seed;
+  h->thr = threshold_of(beta);
+  h->shape = shape_for(L);
+  h->ks = sw::make_key_schedule(seed);
+  cudaGetDevice(&h->device);
+  const sw::TileShape ts = sw::shape_of(h->shape);
+  h->g.L = L;
+  h->g.tiles_x = (L + ts.tw() - 1) / ts.tw();
+  h->g.tiles_y = (L + ts.th - 1) / ts.th;
+  h->g.aligned16 = (L % 16) == 0;
+  const size_t ntiles = (size_t)h->g.tiles_x * h->g.tiles_y;
+  const size_t N = (size_t)L * L;
+  cudaError_t e = cudaSuccess;
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    h->own_stream = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&h->spins, N);
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.tbits, ntiles * 3 * ts.threads() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.nodes, ntiles * ts.max_slots() * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.bslot, ntiles * ts.boundary_sites() * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.bbits, ntiles * ts.bbits_words() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.nslots, ntiles * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->csize, ntiles * ts.max_slots() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->tb.err, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = sw::launch_init(h->spins, L, seed, init == SW_INIT_COLD, h->stream);
+  if (e != cudaSuccess) {
+    const int rc = cuda_fail(e, "sw_create");
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  const int rc = ensure_trace(h, 1024);
+  if (rc != SW_OK) {
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return SW_OK;
+}
+
+int sw_destroy(sw_lattice* h) {
+  if (!h) return SW_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return SW_OK;
+}
+
+int sw_sweep(sw_lattice* h, int32_t n) {
+  if (!h) return fail(SW_EINVAL, "handle is NULL");
+  if (n < 0) return fail(SW_EINVAL, "n must be >= 0");
+  if (n == 0) return SW_OK;
+  int rc = ensure_trace(h, h->t - h->t_base + n);
+  if (rc != SW_OK) return rc;
+  const sw::TileShape ts = sw::shape_of(h->shape);
+  (void)ts;
+  for (int32_t k = 0; k < n; ++k) {
+    sw::SweepArgs a = args_of(h);
+    const int64_t row = h->t - h->t_base;
+    a.em = h->em + 2 * row;
+    a.hist = h->hist + SW_HIST_WORDS * row;
+    a.csize = h->hist_on ? h->csize : nullptr;
+    SW_CUDA(sw::launch_phase1(h->shape, a, h->stream), "phase 1 launch");
+    SW_CUDA(sw::launch_phase2(h->shape, a, h->stream), "phase 2 launch");
+    if (!h->hist_on) a.hist = nullptr;
+    SW_CUDA(sw::launch_phase3(h->shape, a, false, h->stream), "phase 3 launch");
+    if (h->hist_on) SW_CUDA(sw::launch_phase4(h->shape, a, h->stream), "phase 4 launch");
+    h->t += 1;
+  }
+  return SW_OK;
+}
+
+int sw_get_sweep(sw_lattice* h, uint32_t* t_out) {
+  if (!h || !t_out) return fail(SW_EINVAL, "NULL argument");
+  *t_out = (uint32_t)h->t;
+  return SW_OK;
+}
+
+int sw_observables(sw_lattice* h, int64_t first, int64_t count, int64_t* E_host, int64_t* M_host) {
+  if (!h) return fail(SW_EINVAL, "handle is NULL");
+  int rc = range_ok(h, first, count);
+  if (rc != SW_OK) return rc;
+  rc = sync_and_check(h);
+  if (rc != SW_OK) return rc;
+  if (count == 0) return SW_OK;
+  int64_t* tmp = (int64_t*)malloc((size_t)count * 2 * sizeof(int64_t));
+  if (!tmp) return fail(SW_ENOMEM, "host allocation failed");
+  cudaError_t e = cudaMemcpy(tmp, h->em + 2 * (first - h->t_base), (size_t)count * 2 * sizeof(int64_t),
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    free(tmp);
+    return cuda_fail(e, "trace copy");
+  }
+  for (int64_t k = 0; k < count; ++k) {
+    if (E_host) E_host[k] = tmp[2 * k];
+    if (M_host) M_host[k] = tmp[2 * k + 1];
+  }
+  free(tmp);
+  return SW_OK;
+}
+
+int sw_histogram(sw_lattice* h, int32_t enable) {
+  if (!h) return fail(SW_EINVAL, "handle is NULL");
+  h->hist_on = enable != 0;
+  return SW_OK;
+}
+
+int sw_histograms(sw_lattice* h, int64_t first, int64_t count, int64_t* out_host) {
+  if (!h) return fail(SW_EINVAL, "handle is NULL");
+  int rc = range_ok(h, first, count);
+  if (rc != SW_OK) return rc;
+  if (count > 0 && !out_host) return fail(SW_EINVAL, "out_host is NULL");
+  rc = sync_and_check(h);
+  if (rc != SW_OK) return rc;
+  if (count == 0) return SW_OK;
+  SW_CUDA(cudaMemcpy(out_host, h->hist + SW_HIST_WORDS * (first - h->t_base),
+                     (size_t)count * SW_HIST_WORDS * sizeof(int64_t), cudaMemcpyDeviceToHost),
+          "histogram copy");
+  return SW_OK;
+}
+
+int sw_labels(sw_lattice* h, int32_t* out, int32_t out_is_device) {
+  if (!h || !out) return fail(SW_EINVAL, "NULL argument");
+  const size_t N = (size_t)h->L * h->L;
+  int32_t* dst = out;
+  if (!out_is_device) {
+    if (!h->label_buf) SW_CUDA(cudaMalloc(&h->label_buf, N * sizeof(int32_t)), "label buffer");
+    dst = h->label_buf;
+  }
+  sw::SweepArgs a = args_of(h);
+  int rc = run_clusters(h, a);
+  if (rc != SW_OK) return rc;
+  a.labels = dst;
+  SW_CUDA(sw::launch_phase3(h->shape, a, true, h->stream), "phase 3 (labels) launch");
+  if (out_is_device) return SW_OK;
+  SW_CUDA(cudaMemcpyAsync(out, dst, N * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "labels copy");
+  return sync_and_check(h);
+}
+
+int sw_spins(sw_lattice* h, int8_t* out, int32_t out_is_device) {
+  if (!h || !out) return fail(SW_EINVAL, "NULL argument");
+  const size_t N = (size_t)h->L * h->L;
+  SW_CUDA(cudaMemcpyAsync(out, h->spins, N, out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          h->stream),
+          "spins copy");
+  if (out_is_device) return SW_OK;
+  return sync_and_check(h);
+}
+
+int sw_set_state(sw_lattice* h, const int8_t* spins, uint32_t t, int32_t in_is_device) {
+  if (!h || !spins) return fail(SW_EINVAL, "NULL argument");
+  const size_t N = (size_t)h->L * h->L;
+  if (!in_is_device) {
+    for (size_t i = 0; i < N; ++i)
+      if (spins[i] != 1 && spins[i] != -1) return fail(SW_EINVAL, "spin %zu is %d, not +1/-1", i, (int)spins[i]);
+  }
+  SW_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+  SW_CUDA(cudaMemsetAsync(h->tb.err, 0, sizeof(int), h->stream), "error flag reset");
+  SW_CUDA(cudaMemcpyAsync(h->spins, spins, N, in_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          h->stream),
+          "spins copy");
+  if (in_is_device) SW_CUDA(sw::launch_check_spins(h->spins, (int64_t)N, h->tb.err, h->stream), "spin check launch");
+  h->t = t;
+  h->t_base = t;
+  if (!in_is_device) SW_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+  return SW_OK;
+}
+
+int sw_bonds(sw_lattice* h, uint8_t* out_host) {
+  if (!h || !out_host) return fail(SW_EINVAL, "NULL argument");
+  const size_t N = (size_t)h->L * h->L;
+  if (!h->bond_buf) SW_CUDA(cudaMalloc(&h->bond_buf, N), "bond buffer");
+  sw::SweepArgs a = args_of(h);
+  int rc = run_clusters(h, a);
+  if (rc != SW_OK) return rc;
+  SW_CUDA(sw::launch_export_bonds(h->shape, a, h->bond_buf, h->stream), "bond export launch");
+  SW_CUDA(cudaMemcpyAsync(out_host, h->bond_buf, N, cudaMemcpyDeviceToHost, h->stream), "bonds copy");
+  return sync_and_check(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// sw_internal.h -- interface between the C ABI layer (sw_api.cu) and the
+// sweep kernels (sw_kernels.cu). Not installed; not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sw_philox.cuh"
+
+namespace sw {
+
+// Device error flag values (first writer wins).
+enum DeviceError : int {
+  kErrNone = 0,
+  kErrUnionCap = 1,     // a union-find retry loop hit its iteration cap
+  kErrBadSpin = 2,      // sw_set_state from device memory saw a value other than +1/-1
+  kErrSlotOverflow = 3, // more boundary components than slots (cannot happen; checked)
+};
+
+// A tile shape: TW = 32*WPR columns by TH rows, one thread per (row, 32-bit
+// word of the row). Tiles are laid over the L x L lattice from the origin;
+// the last tile column and row may be ragged.
+struct TileShape {
+  int wpr;  // 32-bit words per tile row
+  int th;   // rows per tile
+  int tw() const { return 32 * wpr; }
+  int threads() const { return wpr * th; }
+  int max_slots() const { return 2 * (tw() + th); }     // boundary sites bound the slots
+  int boundary_sites() const { return 2 * th + 2 * tw(); }
+  int bbits_words() const { return 2 * (th / 32) + 2 * (tw() / 32); }
+};
+
+// Shapes compiled into the library; index = variant id.
+constexpr int kNumShapes = 3;
+__host__ __device__ constexpr TileShape shape_of(int v) {
+  return v == 0 ? TileShape{4, 64} : v == 1 ? TileShape{4, 32} : TileShape{2, 64};
+}
+
+// Per-lattice device buffers of the tile pipeline.
+struct TileBuffers {
+  uint32_t* tbits;   // [ntiles][3][threads]: spin bits, east-bond bits, south-bond bits per row-word
+  uint64_t* nodes;   // [ntiles * max_slots]: global union-find, (key << 32) | parent node
+  uint16_t* bslot;   // [ntiles][boundary_sites]: slot of each boundary site (left, right, top, bottom)
+  uint32_t* bbits;   // [ntiles][bbits_words]: E-out bonds, S-out bonds, east halo spins, south halo spins
+  int32_t* nslots;   // [ntiles]
+  int* err;          // device error flag
+};
+
+struct Geometry {
+  int L;
+  int tiles_x, tiles_y;
+  int aligned16;  // rows start on 16-byte boundaries (L % 16 == 0)
+};
+
+struct SweepArgs {
+  Geometry g;
+  uint32_t thr;        // bond threshold (C3)
+  uint32_t t;          // sweep counter (C5, C6)
+  KeySchedule ks;      // Philox key schedule of the seed (C4)
+  TileBuffers tb;
+  const int8_t* spins_in;
+  int8_t* spins_out;   // flip mode: new spins (may alias spins_in)
+  int64_t* em;         // flip mode: E, M accumulators of this sweep (zeroed by phase 1)
+  int64_t* hist;       // flip mode: SW_HIST_WORDS accumulators or nullptr
+  uint32_t* csize;     // flip mode with hist: per-node cluster size accumulators [nodes]
+  int32_t* labels;     // labels mode: int32 [L][L] output
+};
+
+inline int ntiles_of(const Geometry& g) { return g.tiles_x * g.tiles_y; }
+
+// Launchers (sw_kernels.cu). Each returns cudaGetLastError() of its launches.
+cudaError_t launch_init(int8_t* spins, int L, uint64_t seed, int cold, cudaStream_t st);
+cudaError_t launch_check_spins(const int8_t* spins, int64_t n, int* err, cudaStream_t st);
+// Phase 1: bonds + tile-local labelling + boundary slot tables (one CTA per tile).
+cudaError_t launch_phase1(int shape, const SweepArgs& a, cudaStream_t st);
+// Phase 2: union of tile components across bonded tile-boundary edges.
+cudaError_t launch_phase2(int shape, const SweepArgs& a, cudaStream_t st);
+// Phase 3: canonical roots, flips, new spins, E/M (+ statistics), or labels.
+cudaError_t launch_phase3(int shape, const SweepArgs& a, bool labels_mode, cudaStream_t st);
+// Phase 4 (statistics only): log2 histogram of cluster sizes held at global roots.
+cudaError_t launch_phase4(int shape, const SweepArgs& a, cudaStream_t st);
+// Debug: expand the stored bond bits into uint8 [L][L] (bit0 east, bit1 south).
+cudaError_t launch_export_bonds(int shape, const SweepArgs& a, uint8_t* out, cudaStream_t st);
+
+}  // namespace sw

@@ -1,0 +1,58 @@
+// sw_philox.cuh -- device-side Philox-4x32-10 for libsw (conventions C4-C7
+// of include/sw.h).
+//
+// Philox-4x32 is the counter-based generator of Salmon, Moraes, Dror and
+// Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11): each of ten
+// rounds multiplies words 0 and 2 by two fixed 32-bit constants, xors the
+// high halves of the products with the other two words and the round key,
+// and permutes the words; the key advances by two Weyl increments between
+// rounds. The key schedule is uniform across a launch, so the host expands it
+// once into a KeySchedule kernel parameter and the rounds read it from the
+// constant bank instead of adding the increments per call.
+#pragma once
+#include <stdint.h>
+
+namespace sw {
+
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u;
+constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u;
+constexpr uint32_t kPhiloxWeylB = 0xBB67AE85u;
+
+struct KeySchedule {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+// Host and device: round keys of the 10 rounds for a 64-bit seed
+// (key = (seed low word, seed high word)).
+__host__ __device__ inline KeySchedule make_key_schedule(uint64_t seed) {
+  KeySchedule ks;
+  uint32_t a = (uint32_t)(seed & 0xffffffffu), b = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    ks.k0[r] = a;
+    ks.k1[r] = b;
+    a += kPhiloxWeylA;
+    b += kPhiloxWeylB;
+  }
+  return ks;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const KeySchedule& ks) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t pa = (uint64_t)kPhiloxMulA * c.x;
+    const uint64_t pb = (uint64_t)kPhiloxMulB * c.z;
+    c = make_uint4((uint32_t)(pb >> 32) ^ c.y ^ ks.k0[r], (uint32_t)pb,
+                   (uint32_t)(pa >> 32) ^ c.w ^ ks.k1[r], (uint32_t)pa);
+  }
+  return c;
+}
+
+// C6: the cluster rooted at site `root` flips in sweep t iff the top bit of
+// word x0 of block (root, t, 1, 0) is set.
+__device__ __forceinline__ uint32_t flip_bit(uint32_t root, uint32_t t, const KeySchedule& ks) {
+  return philox4x32_10(make_uint4(root, t, 1u, 0u), ks).x >> 31;
+}
+
+}  // namespace sw
