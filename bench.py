@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of one Swendsen-Wang sweep of the 2D Ising model on GB300.
+
+Workload: L = 8192 periodic lattice (67,108,864 sites), beta = 0.44068679
+(beta_c), hot start from seed 3; one step = one full sweep (bonds, tile-local
+and cross-tile cluster labelling, per-cluster flips, E/M reduction).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Our arm prints one JSON line with site-updates/s measured on the device
+(CUDA events on the library's stream, L2 flushed between steps by writing a
+256 MiB buffer), the roofline of the dominant kernel, the end-to-end rate
+through the C ABI with host buffers, the oracle's CPU rate, and the SM clocks
+seen during the timed region. Under torchrun every rank runs its own replica
+(independent chains, no data-path collective: "replicas only"), and rank 0
+reports the whole-job rate.
+
+The reference arm (--impl reference) times the serial CPU oracle on the
+host cores on the same workload, one oracle sweep per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SW site-updates/s at L=8192, β_c; % of HBM roofline; batched vs plain"
+UNIT = "site-updates/s"
+L = 8192
+BETA = 0.44068679
+SEED = 3
+N_SITES = L * L
+FLUSH_BYTES = 256 << 20
+# Tile shape of the default configuration at this L (128 x 64 sites).
+TW, TH = 128, 64
+NB = 2 * TH + 2 * TW
+BBW = 2 * (TH // 32) + 2 * (TW // 32)
+NT = (TW // 32) * TH
+# Algorithmic bytes per full tile ("Bytes per site"); slot nodes
+# (8 bytes per border component) are data dependent and not counted.
+PHASE_BYTES_PER_TILE = {
+    0: (TW * TH + TH + TW) + (3 * NT * 4 + 2 * NB + 4 * BBW + 4),   # spins+halo in; bit masks, slots, tile bits out
+    2: (3 * NT * 4 + 4 + 2 * NB + 2 * (TH + TW) + 4 * BBW) + TW * TH,  # bit masks, slots, halo slots in; spins out
+}
+PHASE_NAMES = {0: "phase1_bonds_tile_ccl", 1: "phase2_merge", 2: "phase3_flip_em", 3: "phase4_hist"}
+SWEEP_MODEL_BYTES_PER_SITE = 10  # read spins, write+read int32 labels, write spins
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="sw_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def cpu_oracle_rate(n_sweeps: int, label: str):
+    """Time the serial oracle as it stands on n_sweeps of the workload."""
+    import oracle
+    oracle.build()
+    s0 = oracle.init(L, SEED)
+    t0 = time.perf_counter()
+    oracle.run(L, BETA, SEED, n_sweeps, spins=s0)
+    dt = time.perf_counter() - t0
+    return {"value": N_SITES * n_sweeps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_sweeps} {label} of L={L} beta={BETA} from the oracle's own hot start "
+                      f"({dt:.1f} s, serial C, {platform.machine()})"}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# -------------------------------------------------------------- reference
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    s = oracle.init(L, SEED)
+    t = 0
+    for _ in range(args.warmup):
+        s, _, _, _ = oracle.run(L, BETA, SEED, 1, spins=s, t0=t)
+        t += 1
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        s, _, _, _ = oracle.run(L, BETA, SEED, 1, spins=s, t0=t)
+        times.append(time.perf_counter() - t0)
+        t += 1
+    total = sum(times)
+    value = N_SITES * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8/u32",
+        "data": "synthetic (Philox hot start, seed 3)",
+        "config": {"workload": f"L{L} beta_c={BETA} hot start seed {SEED}, one SW sweep per step",
+                   "L": L, "beta": BETA, "seed": SEED},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} oracle sweeps of L={L} (serial C, one host core, "
+                                   f"{platform.machine()})"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    import paper_2302_14720_gb300 as sw
+
+    hbm_peak, peak_kind = peaks()
+    # One non-default stream carries the library's kernels, the L2 flushes and
+    # the timing events, so the events bracket exactly the sweep's kernels.
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    seed = SEED + rank  # rank 0 runs the configured chain; other ranks are independent replicas
+    lat = sw.Lattice(L, BETA, seed, sw.SW_INIT_HOT, stream=stream.cuda_stream)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    # warm-up (each step preceded by an L2 flush, as in the timed loop)
+    for k in range(args.warmup):
+        flush.fill_(k & 0xFF)
+        lat.sweep(1)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_first = lat.t
+    clocks = ClockSampler(local) if rank == 0 else None
+    sw.sw_timing(lat.h, True)
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_((k + 7) & 0xFF)
+        starts[k].record(stream)
+        lat.sweep(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clock_info = clocks.stop() if clocks else None
+    phase_ms, phase_n = sw.sw_timing_read(lat.h)
+    sw.sw_timing(lat.h, False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    E, M = lat.observables(t_first, args.steps)
+    assert (np.abs(E) <= 2 * N_SITES).all() and (np.abs(M) <= N_SITES).all()
+    max_ms = max_over_ranks(total_ms, world)
+    value = world * N_SITES * args.steps / (max_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (largest summed device time)
+    ntiles = (L // TW) * (L // TH)
+    dom = max((0, 1, 2), key=lambda p: phase_ms[p])
+    dom_avg_ms = phase_ms[dom] / max(phase_n[dom], 1)
+    dom_bytes = PHASE_BYTES_PER_TILE.get(dom, 0) * ntiles
+    achieved = dom_bytes / (dom_avg_ms / 1e3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "dram_traffic_L8192.json")
+    if os.path.exists(tpath):
+        tr = json.load(open(tpath))
+        if tr.get("kernel") == PHASE_NAMES[dom] and tr.get("source_hash") == sw_source_hash():
+            traffic = tr.get("bytes_per_launch")
+    roofline = {"bound": "hbm", "kernel": PHASE_NAMES[dom], "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                "peak_kind": peak_kind, "bytes_per_launch": dom_bytes, "avg_launch_ms": dom_avg_ms}
+    phases = {PHASE_NAMES[p]: {"ms_per_launch": phase_ms[p] / max(phase_n[p], 1), "launches": int(phase_n[p])}
+              for p in range(4) if phase_n[p]}
+    sweep_roofline_su_s = hbm_peak * 1e9 / SWEEP_MODEL_BYTES_PER_SITE
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    host = torch.empty((L, L), dtype=torch.int8, pin_memory=True)
+    host_np = host.numpy()
+    host_np[...] = lat.spins()
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e_times = []
+    t = lat.t
+    for k in range(e2e_steps + 1):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sw.sw_set_state(lat.h, host_np, t)            # H2D: the step's input state
+        lat.sweep(1)
+        Ek, Mk = lat.observables(t, 1)                 # D2H: the step's E and M (synchronises)
+        dt = time.perf_counter() - t0
+        if k > 0:
+            e2e_times.append(dt)
+        t += 1
+    e2e_value = world * N_SITES * len(e2e_times) / max_over_ranks(sum(e2e_times), world)
+    lat.close()
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(args.cpu_sweeps, "sweeps")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int8/u32",
+        "data": "synthetic (Philox hot start, seed 3 + rank)",
+        "config": {"workload": f"L{L} beta_c={BETA} hot start seed {SEED}, one SW sweep per step",
+                   "L": L, "beta": BETA, "seed": SEED, "tile": f"{TW}x{TH}",
+                   "l2": "flushed between steps (256 MiB write), inputs 64 MiB < L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "sweep_vs_10B_per_site_hbm_model": {"roofline_su_s": sweep_roofline_su_s, "frac": value / world / sweep_roofline_su_s},
+        "phases": phases,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N_SITES, "d2h_bytes_per_step": 16,
+                "steps": len(e2e_times), "ms_per_step": 1e3 * statistics.mean(e2e_times)},
+        "gpu_launches": int(phase_n[:3].sum()),
+        "clocks": clock_info,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def sw_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2302_14720_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sweeps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -156,17 +156,32 @@ int sw_labels(sw_lattice* h, int32_t* out, int32_t out_is_device);
  * for sw_labels. */
 int sw_spins(sw_lattice* h, int8_t* out, int32_t out_is_device);
 
-/* Replace the state: spins int8 [L][L] (every value must be +1 or -1, else
- * SW_EINVAL for host input; device input is checked on the device and
- * reported as SW_EINVAL by the next synchronising call) and the sweep
- * counter t. Clears the trace (its start becomes t). Used to resume a run
- * from a checkpoint and for spot checks. */
+/* Replace the state: spins int8 [L][L] and the sweep counter t. Every
+ * value must be +1 or -1. Host input is copied to a device staging buffer
+ * and checked there before it replaces the state: the call synchronises and
+ * returns SW_EINVAL, leaving the state untouched, if a value is invalid.
+ * Device input is copied and checked asynchronously; a bad value is
+ * reported as SW_EINVAL by the next synchronising call. Clears the trace
+ * (its start becomes t). Used to resume a run from a checkpoint. */
 int sw_set_state(sw_lattice* h, const int8_t* spins, uint32_t t, int32_t in_is_device);
 
 /* Debug export of the bonds that the NEXT sweep (counter t) draws from the
  * current spins (§2.1): out_host uint8 [L][L], bit0 = east bond,
  * bit1 = south bond. Synchronises. The state is not changed. */
 int sw_bonds(sw_lattice* h, uint8_t* out_host);
+
+/* Per-phase device timing of the sweeps that follow: with enable = 1 every
+ * phase launch of sw_sweep is bracketed by CUDA events on the handle's
+ * stream (accumulators cleared); enable = 0 stops recording. Phases:
+ * 0 = bonds + tile-local clusters, 1 = cross-tile merge, 2 = flips + E/M,
+ * 3 = cluster statistics. Not part of the paper: measurement support. */
+int sw_timing(sw_lattice* h, int32_t enable);
+
+/* Synchronise, then report for each of the 4 phases the summed device time
+ * in milliseconds (ms_out[4]) and the number of kernel launches
+ * (launches_out[4]) recorded since sw_timing(h, 1). Either pointer may be
+ * NULL. */
+int sw_timing_read(sw_lattice* h, double* ms_out, int64_t* launches_out);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* sw_last_error(void);

@@ -49,6 +49,8 @@ SIGNATURES = {
     "sw_spins": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "sw_set_state": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_int32]),
     "sw_bonds": (ctypes.c_int, [_P, _P]),
+    "sw_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sw_timing_read": (ctypes.c_int, [_P, _P, _P]),
     "sw_last_error": (ctypes.c_char_p, []),
 }
 
@@ -91,6 +93,8 @@ def sw_threshold(beta: float) -> int:
 
 
 def sw_create(L: int, beta: float, seed: int, init: int = SW_INIT_HOT, stream: int | None = None) -> int:
+    """stream: a cudaStream_t handle; None lets the library create its own. The
+    legacy default stream (handle 0) cannot be passed: it reads as None."""
     h = ctypes.c_void_p()
     _check(_lib.sw_create(int(L), float(beta), int(seed) & 0xFFFFFFFFFFFFFFFF, int(init),
                           ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)), "sw_create")
@@ -160,6 +164,18 @@ def sw_bonds(h: int, L: int) -> np.ndarray:
     out = np.zeros((L, L), np.uint8)
     _check(_lib.sw_bonds(h, _host_ptr(out)), "sw_bonds")
     return out
+
+
+def sw_timing(h: int, enable: bool) -> None:
+    _check(_lib.sw_timing(h, 1 if enable else 0), "sw_timing")
+
+
+def sw_timing_read(h: int):
+    """(ms per phase float64[4], launches per phase int64[4]) since sw_timing(h, True)."""
+    ms = np.zeros(4, np.float64)
+    n = np.zeros(4, np.int64)
+    _check(_lib.sw_timing_read(h, _host_ptr(ms), _host_ptr(n)), "sw_timing_read")
+    return ms, n
 
 
 def sw_last_error() -> str:

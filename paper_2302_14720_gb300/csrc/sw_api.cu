@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "sw.h"
 #include "sw_internal.h"
@@ -82,16 +83,71 @@ struct sw_lattice {
   int64_t* hist = nullptr;  // [cap][SW_HIST_WORDS]
   int32_t* label_buf = nullptr;
   uint8_t* bond_buf = nullptr;
+  int8_t* staging = nullptr;  // host sw_set_state lands here and is checked first
+  int* check_flag = nullptr;
+  // per-phase timing (sw_timing)
+  bool timing_on = false;
+  struct Mark {
+    int phase;
+    cudaEvent_t start, stop;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> event_pool;
+  double phase_ms[4] = {0, 0, 0, 0};
+  int64_t phase_launches[4] = {0, 0, 0, 0};
 };
 
 namespace {
 
 void free_all(sw_lattice* h) {
   void* ptrs[] = {h->spins, h->tb.tbits, h->tb.nodes, h->tb.bslot, h->tb.bbits, h->tb.nslots, h->tb.err,
-                  h->csize, h->em, h->hist, h->label_buf, h->bond_buf};
+                  h->csize, h->em, h->hist, h->label_buf, h->bond_buf, h->staging, h->check_flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (auto& m : h->marks) {
+    cudaEventDestroy(m.start);
+    cudaEventDestroy(m.stop);
+  }
+  for (cudaEvent_t ev : h->event_pool) cudaEventDestroy(ev);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+cudaError_t take_event(sw_lattice* h, cudaEvent_t* ev) {
+  if (!h->event_pool.empty()) {
+    *ev = h->event_pool.back();
+    h->event_pool.pop_back();
+    return cudaSuccess;
+  }
+  return cudaEventCreate(ev);
+}
+
+// Launch one phase, bracketed by timing events when sw_timing is on.
+template <typename F>
+cudaError_t timed_phase(sw_lattice* h, int phase, F&& launch) {
+  if (!h->timing_on) return launch();
+  sw_lattice::Mark m{phase, nullptr, nullptr};
+  cudaError_t e = take_event(h, &m.start);
+  if (e == cudaSuccess) e = take_event(h, &m.stop);
+  if (e == cudaSuccess) e = cudaEventRecord(m.start, h->stream);
+  if (e == cudaSuccess) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(m.stop, h->stream);
+  if (e == cudaSuccess) h->marks.push_back(m);
+  return e;
+}
+
+// Fold recorded event pairs into the per-phase sums (events must be complete).
+cudaError_t drain_marks(sw_lattice* h) {
+  for (auto& m : h->marks) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&ms, m.start, m.stop);
+    if (e != cudaSuccess) return e;
+    h->phase_ms[m.phase] += ms;
+    h->phase_launches[m.phase] += 1;
+    h->event_pool.push_back(m.start);
+    h->event_pool.push_back(m.stop);
+  }
+  h->marks.clear();
+  return cudaSuccess;
 }
 
 sw::SweepArgs args_of(const sw_lattice* h) {
@@ -261,11 +317,12 @@ int sw_sweep(sw_lattice* h, int32_t n) {
     a.em = h->em + 2 * row;
     a.hist = h->hist + SW_HIST_WORDS * row;
     a.csize = h->hist_on ? h->csize : nullptr;
-    SW_CUDA(sw::launch_phase1(h->shape, a, h->stream), "phase 1 launch");
-    SW_CUDA(sw::launch_phase2(h->shape, a, h->stream), "phase 2 launch");
+    SW_CUDA(timed_phase(h, 0, [&] { return sw::launch_phase1(h->shape, a, h->stream); }), "phase 1 launch");
+    SW_CUDA(timed_phase(h, 1, [&] { return sw::launch_phase2(h->shape, a, h->stream); }), "phase 2 launch");
     if (!h->hist_on) a.hist = nullptr;
-    SW_CUDA(sw::launch_phase3(h->shape, a, false, h->stream), "phase 3 launch");
-    if (h->hist_on) SW_CUDA(sw::launch_phase4(h->shape, a, h->stream), "phase 4 launch");
+    SW_CUDA(timed_phase(h, 2, [&] { return sw::launch_phase3(h->shape, a, false, h->stream); }), "phase 3 launch");
+    if (h->hist_on)
+      SW_CUDA(timed_phase(h, 3, [&] { return sw::launch_phase4(h->shape, a, h->stream); }), "phase 4 launch");
     h->t += 1;
   }
   return SW_OK;
@@ -351,19 +408,52 @@ int sw_spins(sw_lattice* h, int8_t* out, int32_t out_is_device) {
 int sw_set_state(sw_lattice* h, const int8_t* spins, uint32_t t, int32_t in_is_device) {
   if (!h || !spins) return fail(SW_EINVAL, "NULL argument");
   const size_t N = (size_t)h->L * h->L;
-  if (!in_is_device) {
-    for (size_t i = 0; i < N; ++i)
-      if (spins[i] != 1 && spins[i] != -1) return fail(SW_EINVAL, "spin %zu is %d, not +1/-1", i, (int)spins[i]);
+  if (in_is_device) {
+    SW_CUDA(cudaMemsetAsync(h->tb.err, 0, sizeof(int), h->stream), "error flag reset");
+    SW_CUDA(cudaMemcpyAsync(h->spins, spins, N, cudaMemcpyDeviceToDevice, h->stream), "spins copy");
+    SW_CUDA(sw::launch_check_spins(h->spins, (int64_t)N, h->tb.err, h->stream), "spin check launch");
+  } else {
+    if (!h->staging) SW_CUDA(cudaMalloc(&h->staging, N), "staging buffer");
+    if (!h->check_flag) SW_CUDA(cudaMalloc(&h->check_flag, sizeof(int)), "check flag");
+    SW_CUDA(cudaMemsetAsync(h->check_flag, 0, sizeof(int), h->stream), "check flag reset");
+    SW_CUDA(cudaMemcpyAsync(h->staging, spins, N, cudaMemcpyHostToDevice, h->stream), "spins copy");
+    SW_CUDA(sw::launch_check_spins(h->staging, (int64_t)N, h->check_flag, h->stream), "spin check launch");
+    int bad = 0;
+    SW_CUDA(cudaMemcpyAsync(&bad, h->check_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "check flag read");
+    SW_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    if (bad) return fail(SW_EINVAL, "sw_set_state: spins contain values other than +1/-1");
+    int8_t* old = h->spins;
+    h->spins = h->staging;
+    h->staging = old;
+    SW_CUDA(cudaMemsetAsync(h->tb.err, 0, sizeof(int), h->stream), "error flag reset");
   }
-  SW_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
-  SW_CUDA(cudaMemsetAsync(h->tb.err, 0, sizeof(int), h->stream), "error flag reset");
-  SW_CUDA(cudaMemcpyAsync(h->spins, spins, N, in_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                          h->stream),
-          "spins copy");
-  if (in_is_device) SW_CUDA(sw::launch_check_spins(h->spins, (int64_t)N, h->tb.err, h->stream), "spin check launch");
   h->t = t;
   h->t_base = t;
-  if (!in_is_device) SW_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+  return SW_OK;
+}
+
+int sw_timing(sw_lattice* h, int32_t enable) {
+  if (!h) return fail(SW_EINVAL, "handle is NULL");
+  if (enable) {
+    SW_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    SW_CUDA(drain_marks(h), "timing events");
+    for (int k = 0; k < 4; ++k) {
+      h->phase_ms[k] = 0.0;
+      h->phase_launches[k] = 0;
+    }
+  }
+  h->timing_on = enable != 0;
+  return SW_OK;
+}
+
+int sw_timing_read(sw_lattice* h, double* ms_out, int64_t* launches_out) {
+  if (!h) return fail(SW_EINVAL, "handle is NULL");
+  SW_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+  SW_CUDA(drain_marks(h), "timing events");
+  for (int k = 0; k < 4; ++k) {
+    if (ms_out) ms_out[k] = h->phase_ms[k];
+    if (launches_out) launches_out[k] = h->phase_launches[k];
+  }
   return SW_OK;
 }
 
