@@ -183,6 +183,37 @@ int sw_timing(sw_lattice* h, int32_t enable);
  * NULL. */
 int sw_timing_read(sw_lattice* h, double* ms_out, int64_t* launches_out);
 
+/* Largest side accepted by sw_sweep_noalloc. */
+#define SW_NOALLOC_MAX_L 1024
+
+/* Allocation-free sweep. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- a host framework
+ * whose allocator has already reserved the GPU's memory, a plugin host that
+ * forbids device allocation, or a latency-critical loop that cannot accept
+ * cudaMalloc's implicit device-wide synchronisation. It runs the same sweep
+ * as sw_sweep (same conventions C1-C10, bit-identical results) without a
+ * handle and without allocating anything.
+ *  spins  : device int8 [L][L] (+1/-1), the state; read and updated in place.
+ *  L      : 2 <= L <= SW_NOALLOC_MAX_L, else SW_EINVAL.
+ *  beta   : finite, >= 0 (C2, C3).
+ *  seed   : Philox key (C4).
+ *  t0, n  : sweeps use counters t0 .. t0+n-1 (C8); n >= 0.
+ *  em     : device int64 [n][2], output: E and M after each sweep (C10).
+ *  err    : device int32 [1], output: set to 0 by the call, then to a
+ *           nonzero code if a capped device retry loop gave up.
+ *  stream : cudaStream_t for all work (NULL = the legacy default stream).
+ * The kernels' working buffers live in one file-scope __device__ array of
+ * under 1 MiB that every GPU loading the library holds until exit. The first
+ * call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and its contents persist between calls, so calls
+ * that overlap on the GPU (other streams, other host threads) race and
+ * corrupt each other's results: serialise them. Work is asynchronous on the
+ * stream; argument errors return SW_EINVAL before anything is enqueued,
+ * launch failures SW_ECUDA. Calls no cudaMalloc/cudaFree. */
+int sw_sweep_noalloc(int8_t* spins, int32_t L, double beta, uint64_t seed, uint32_t t0, int32_t n,
+                     int64_t* em, int32_t* err, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* sw_last_error(void);
 

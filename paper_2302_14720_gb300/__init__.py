@@ -51,8 +51,11 @@ SIGNATURES = {
     "sw_bonds": (ctypes.c_int, [_P, _P]),
     "sw_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sw_timing_read": (ctypes.c_int, [_P, _P, _P]),
+    "sw_sweep_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                        ctypes.c_int32, _P, _P, _P]),
     "sw_last_error": (ctypes.c_char_p, []),
 }
+SW_NOALLOC_MAX_L = 1024
 
 
 class SWError(RuntimeError):
@@ -176,6 +179,16 @@ def sw_timing_read(h: int):
     n = np.zeros(4, np.int64)
     _check(_lib.sw_timing_read(h, _host_ptr(ms), _host_ptr(n)), "sw_timing_read")
     return ms, n
+
+
+def sw_sweep_noalloc(spins_dev: int, L: int, beta: float, seed: int, t0: int, n: int, em_dev: int,
+                     err_dev: int, stream: int | None = None) -> None:
+    """Allocation-free sweep on caller-owned device buffers (see include/sw.h):
+    spins int8 [L][L] updated in place, em int64 [n][2] and err int32 [1]
+    outputs, all device pointers; asynchronous on `stream`."""
+    _check(_lib.sw_sweep_noalloc(ctypes.c_void_p(spins_dev), int(L), float(beta), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                 int(t0) & 0xFFFFFFFF, int(n), ctypes.c_void_p(em_dev), ctypes.c_void_p(err_dev),
+                                 ctypes.c_void_p(stream) if stream else None), "sw_sweep_noalloc")
 
 
 def sw_last_error() -> str:

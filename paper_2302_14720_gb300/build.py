@@ -1,6 +1,6 @@
 """Build libsw.so (the CUDA kernels and the C ABI) for sm_103a with nvcc.
 
-The library is built in-tree into paper_2302_14720_gb300/_build/. The two
+The library is built in-tree into paper_2302_14720_gb300/_build/. The
 translation units compile in parallel; cudart is linked statically so the
 library needs nothing but the driver at run time.
 """
@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libsw.so")
-SOURCES = ["sw_kernels.cu", "sw_api.cu"]
+SOURCES = ["sw_kernels.cu", "sw_api.cu", "sw_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC]

@@ -61,6 +61,10 @@ int shape_for(int L) {
 
 }  // namespace
 
+namespace sw {
+int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace sw
+
 struct sw_lattice {
   int L = 0;
   double beta = 0.0;

@@ -67,6 +67,9 @@ struct SweepArgs {
 
 inline int ntiles_of(const Geometry& g) { return g.tiles_x * g.tiles_y; }
 
+// Set the thread's last error message (sw_last_error) and return code.
+int record_error(int code, const char* msg);
+
 // Launchers (sw_kernels.cu). Each returns cudaGetLastError() of its launches.
 cudaError_t launch_init(int8_t* spins, int L, uint64_t seed, int cold, cudaStream_t st);
 cudaError_t launch_check_spins(const int8_t* spins, int64_t n, int* err, cudaStream_t st);
