@@ -42,16 +42,20 @@ BETA = 0.44068679
 SEED = 3
 N_SITES = L * L
 FLUSH_BYTES = 256 << 20
-# Tile shape of the default configuration at this L (128 x 64 sites).
+# Tile shape of the default configuration at this L (128 x 64 sites, 2-row strips).
 TW, TH = 128, 64
 NB = 2 * TH + 2 * TW
 BBW = 2 * (TH // 32) + 2 * (TW // 32)
-NT = (TW // 32) * TH
+RW = (TW // 32) * TH  # 32-site row-words per tile
 # Algorithmic bytes per full tile ("Bytes per site"); slot nodes
 # (8 bytes per border component) are data dependent and not counted.
 PHASE_BYTES_PER_TILE = {
-    0: (TW * TH + TH + TW) + (3 * NT * 4 + 2 * NB + 4 * BBW + 4),   # spins+halo in; bit masks, slots, tile bits out
-    2: (3 * NT * 4 + 4 + 2 * NB + 2 * (TH + TW) + 4 * BBW) + TW * TH,  # bit masks, slots, halo slots in; spins out
+    # spins + halo in; spin/east/south masks, 16-bit tile roots, border-root
+    # masks, border slots, tile bits, slot count out
+    0: (TW * TH + TH + TW) + (3 * RW * 4 + 2 * TW * TH + 4 * RW + 2 * NB + 4 * BBW + 4),
+    # spin/east masks, roots, border-root masks, slot count, tile bits,
+    # neighbours' halo slots in; spins out
+    2: (2 * RW * 4 + 2 * TW * TH + 4 * RW + 4 + 4 * BBW + 2 * (TH + TW)) + TW * TH,
 }
 PHASE_NAMES = {0: "phase1_bonds_tile_ccl", 1: "phase2_merge", 2: "phase3_flip_em", 3: "phase4_hist"}
 SWEEP_MODEL_BYTES_PER_SITE = 10  # read spins, write+read int32 labels, write spins
@@ -295,7 +299,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int8/u32",
         "data": "synthetic (Philox hot start, seed 3 + rank)",
         "config": {"workload": f"L{L} beta_c={BETA} hot start seed {SEED}, one SW sweep per step",
-                   "L": L, "beta": BETA, "seed": SEED, "tile": f"{TW}x{TH}",
+                   "L": L, "beta": BETA, "seed": SEED, "tile": f"{TW}x{TH}, 2-row strips",
                    "l2": "flushed between steps (256 MiB write), inputs 64 MiB < L2",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,

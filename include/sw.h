@@ -203,7 +203,7 @@ int sw_timing_read(sw_lattice* h, double* ms_out, int64_t* launches_out);
  *           nonzero code if a capped device retry loop gave up.
  *  stream : cudaStream_t for all work (NULL = the legacy default stream).
  * The kernels' working buffers live in one file-scope __device__ array of
- * under 1 MiB that every GPU loading the library holds until exit. The first
+ * under 4 MiB that every GPU loading the library holds until exit. The first
  * call on a device looks up that array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array and its contents persist between calls, so calls

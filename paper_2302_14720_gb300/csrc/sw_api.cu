@@ -56,7 +56,7 @@ int shape_for(int L) {
     const int v = atoi(env);
     if (v >= 0 && v < sw::kNumShapes) return v;
   }
-  return L <= 64 ? 2 : 0;
+  return L <= 64 ? 2 : 6;
 }
 
 }  // namespace
@@ -104,7 +104,7 @@ struct sw_lattice {
 namespace {
 
 void free_all(sw_lattice* h) {
-  void* ptrs[] = {h->spins, h->tb.tbits, h->tb.nodes, h->tb.bslot, h->tb.bbits, h->tb.nslots, h->tb.err,
+  void* ptrs[] = {h->spins, h->tb.tbits, h->tb.roots, h->tb.bmask, h->tb.nodes, h->tb.bslot, h->tb.bbits, h->tb.nslots, h->tb.err,
                   h->csize, h->em, h->hist, h->label_buf, h->bond_buf, h->staging, h->check_flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -274,7 +274,9 @@ int sw_create(int32_t L, double beta, uint64_t seed, int32_t init, void* stream,
     h->own_stream = e == cudaSuccess;
   }
   if (e == cudaSuccess) e = cudaMalloc(&h->spins, N);
-  if (e == cudaSuccess) e = cudaMalloc(&h->tb.tbits, ntiles * 3 * ts.threads() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.tbits, ntiles * 3 * ts.row_words() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.roots, ntiles * ts.sites() * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.bmask, ntiles * ts.row_words() * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.nodes, ntiles * ts.max_slots() * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.bslot, ntiles * ts.boundary_sites() * sizeof(uint16_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.bbits, ntiles * ts.bbits_words() * sizeof(uint32_t));

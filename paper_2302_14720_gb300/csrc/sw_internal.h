@@ -16,28 +16,40 @@ enum DeviceError : int {
   kErrSlotOverflow = 3, // more boundary components than slots (cannot happen; checked)
 };
 
-// A tile shape: TW = 32*WPR columns by TH rows, one thread per (row, 32-bit
-// word of the row). Tiles are laid over the L x L lattice from the origin;
-// the last tile column and row may be ragged.
+// A tile shape: TW = 32*WPR columns by TH rows. Each thread owns one 32-site
+// word column of an H-row strip of the tile (WPR * TH/H threads per tile).
+// Tiles are laid over the L x L lattice from the origin; the last tile
+// column and row may be ragged.
 struct TileShape {
   int wpr;  // 32-bit words per tile row
   int th;   // rows per tile
+  int h;    // rows per thread strip
   int tw() const { return 32 * wpr; }
-  int threads() const { return wpr * th; }
+  int row_words() const { return wpr * th; }
+  int sites() const { return tw() * th; }
+  int threads() const { return wpr * (th / h); }
   int max_slots() const { return 2 * (tw() + th); }     // boundary sites bound the slots
   int boundary_sites() const { return 2 * th + 2 * tw(); }
   int bbits_words() const { return 2 * (th / 32) + 2 * (tw() / 32); }
 };
 
 // Shapes compiled into the library; index = variant id.
-constexpr int kNumShapes = 3;
+constexpr int kNumShapes = 7;
 __host__ __device__ constexpr TileShape shape_of(int v) {
-  return v == 0 ? TileShape{4, 64} : v == 1 ? TileShape{4, 32} : TileShape{2, 64};
+  return v == 0   ? TileShape{4, 64, 4}
+         : v == 1 ? TileShape{4, 64, 8}
+         : v == 2 ? TileShape{2, 64, 4}
+         : v == 3 ? TileShape{8, 64, 4}
+         : v == 4 ? TileShape{4, 128, 4}
+         : v == 5 ? TileShape{8, 64, 8}
+                  : TileShape{4, 64, 2};
 }
 
 // Per-lattice device buffers of the tile pipeline.
 struct TileBuffers {
-  uint32_t* tbits;   // [ntiles][3][threads]: spin bits, east-bond bits, south-bond bits per row-word
+  uint32_t* tbits;   // [ntiles][3][row_words]: spin bits, east-bond bits, south-bond bits per row-word
+  uint16_t* roots;   // [ntiles][sites]: tile-local root of every run start (phase 1 -> phase 3)
+  uint32_t* bmask;   // [ntiles][row_words]: bit set at every tile root that touches the tile border
   uint64_t* nodes;   // [ntiles * max_slots]: global union-find, (key << 32) | parent node
   uint16_t* bslot;   // [ntiles][boundary_sites]: slot of each boundary site (left, right, top, bottom)
   uint32_t* bbits;   // [ntiles][bbits_words]: E-out bonds, S-out bonds, east halo spins, south halo spins

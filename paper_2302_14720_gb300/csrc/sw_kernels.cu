@@ -1,19 +1,26 @@
 // sw_kernels.cu -- the Swendsen-Wang sweep on sm_103a.
 //
-// One sweep (paper §2) runs as three kernels over square-ish tiles of
-// TW = 32*WPR columns by TH rows; one thread owns one 32-site word of one
-// tile row and keeps its sites as bit masks (bit k = site x0+32w+k).
+// One sweep (paper §2) runs as three kernels over tiles of TW = 32*WPR
+// columns by TH rows. Sites are handled as bit masks, 32 per 32-bit word
+// (bit k = site x0+32w+k). Each thread owns one word column w of an H-row
+// strip of the tile and scans it top to bottom.
 //
 //  phase 1 (bonds §2.1 + tile-local clusters §2.3)
 //    - int8 spins -> sign bits; the tile's east halo column and south halo
 //      row are read too, so every east/south bond of the tile can be drawn;
 //    - Philox-4x32-10 block (site>>1, t, 0, 0) gives the east and south words
 //      of two consecutive sites (C5); bond iff equal spins and word < thr;
-//    - union-find in shared memory over word-local runs of east bonds: a run
-//      is a maximal stretch of east-bonded sites inside one word, its start
-//      is its node; south bonds and word-crossing east bonds unite runs
-//      (atomicMin towards the smaller index, so each tile component's root
-//      is its smallest site -- the "lowest value label" of §2.3);
+//    - clusters: nodes are word-local runs (maximal stretches of east bonds
+//      inside one word, named by their first site). Inside a strip the
+//      thread scans rows in order, as in Hoshen-Kopelman labelling: a run
+//      with a south bond from the row above takes that run's root, a run
+//      reached from two roots merges them (the larger index points to the
+//      smaller). Parents are 16-bit, in shared memory, and owned by the
+//      scanning thread, so the scan needs no atomics. Bonds across strip
+//      boundaries and across words are united afterwards with atomic
+//      minimum (the larger root points to the smaller), so each tile
+//      component's root is its smallest site -- the "lowest value label"
+//      of §2.3;
 //    - every tile component that touches the tile border gets a slot; slot
 //      nodes are initialised in a global 64-bit union-find whose entries are
 //      (key << 32 | parent node), key = smallest global site index of the
@@ -27,7 +34,7 @@
 //      unites the two slot nodes with 64-bit atomicMin; consecutive edges
 //      joining the same two slots are skipped.
 //  phase 3 (new spins §2.4 + E/M, or canonical labels)
-//    - rebuilds the tile-local union-find from the stored bit masks, takes
+//    - rebuilds the tile-local clusters from the stored bit masks, takes
 //      each border component's global root (its key is the cluster's
 //      canonical label, C9) and each inner component's own root;
 //    - one Philox block (root, t, 1, 0) per root decides the flip (C6); the
@@ -99,8 +106,52 @@ __device__ __forceinline__ void store_spin_bits(int8_t* p, uint32_t bits, int nb
 }
 
 // ------------------------------------------------ shared-memory union-find
+// Parents are 16-bit local site indices (par[x] <= x; roots point to
+// themselves).
 
-__device__ __forceinline__ int find_local(const volatile int* par, int x) {
+// Replace the 16-bit entry at p by v if it is larger; returns the old entry.
+__device__ __forceinline__ uint32_t atomic_min_u16(uint16_t* p, uint32_t v) {
+  unsigned int* w = reinterpret_cast<unsigned int*>(reinterpret_cast<uintptr_t>(p) & ~uintptr_t(3));
+  const int sh = (reinterpret_cast<uintptr_t>(p) & 2u) ? 16 : 0;
+  unsigned int old = *reinterpret_cast<volatile unsigned int*>(w);
+  for (;;) {
+    const uint32_t cur = (old >> sh) & 0xFFFFu;
+    if (cur <= v) return cur;
+    const unsigned int nw = (old & ~(0xFFFFu << sh)) | (v << sh);
+    const unsigned int seen = atomicCAS(w, old, nw);
+    if (seen == old) return cur;
+    old = seen;
+  }
+}
+
+// Root of x while no other thread writes the entries on its path (the
+// strip scan); halves the path.
+__device__ __forceinline__ int find_own(uint16_t* par, int x) {
+  for (;;) {
+    const int p = par[x];
+    if (p == x) return x;
+    const int gp = par[p];
+    if (gp == p) return p;
+    par[x] = (uint16_t)gp;
+    x = gp;
+  }
+}
+
+// Root of x while other threads may be uniting: path halving with plain
+// 16-bit stores of ancestors (a lost halving store leaves a valid pointer).
+__device__ __forceinline__ int find_shared(volatile uint16_t* par, int x) {
+  for (;;) {
+    const int p = par[x];
+    if (p == x) return x;
+    const int gp = par[p];
+    if (gp == p) return p;
+    par[x] = (uint16_t)gp;
+    x = gp;
+  }
+}
+
+// Root of x once all unions are done: read-only walk.
+__device__ __forceinline__ int find_final(const volatile uint16_t* par, int x) {
   int p = par[x];
   while (p != x) {
     x = p;
@@ -109,20 +160,20 @@ __device__ __forceinline__ int find_local(const volatile int* par, int x) {
   return x;
 }
 
-// Entries only ever decrease (par[x] <= x), so finds terminate; a failed
-// atomicMin means another thread linked `a` first, and the loop carries on
+// Lock-free union: the larger root is hung under the smaller one; a failed
+// minimum means another thread linked `a` first, and the loop carries on
 // with a's new parent. The cap only guards against corrupted memory.
-__device__ void unite_local(int* par, int a, int b, int* err) {
+__device__ void unite_shared(uint16_t* par, int a, int b, int* err) {
   for (int it = 0; it < kUnionCap; ++it) {
-    a = find_local(par, a);
-    b = find_local(par, b);
+    a = find_shared(par, a);
+    b = find_shared(par, b);
     if (a == b) return;
     if (a < b) {
       const int tmp = a;
       a = b;
       b = tmp;
     }
-    const int old = atomicMin(&par[a], b);
+    const int old = (int)atomic_min_u16(&par[a], (uint32_t)b);
     if (old == a) return;
     a = old;
   }
@@ -177,18 +228,21 @@ __device__ void unite_global(uint64_t* nodes, uint32_t a, uint32_t b, int* err) 
 
 // ----------------------------------------------------------- tile helpers
 
-template <int WPR, int TH>
+template <int WPR, int TH, int H>
 struct Tile {
   static constexpr int TW = 32 * WPR;
-  static constexpr int NT = WPR * TH;
+  static constexpr int NS = TH / H;                 // strips per tile
+  static constexpr int NT = WPR * NS;               // threads per tile
+  static constexpr int RW = WPR * TH;               // row-words per tile
   static constexpr int NB = 2 * TH + 2 * TW;        // border sites: left, right, top, bottom
   static constexpr int MS = 2 * (TW + TH);          // slots per tile
   static constexpr int BBW = 2 * (TH / 32) + 2 * (TW / 32);
   static constexpr int OFF_EOUT = 0, OFF_SOUT = TH / 32, OFF_HE = TH / 32 + TW / 32,
                        OFF_HS = 2 * (TH / 32) + TW / 32;
-  static_assert(TH % 32 == 0, "TH must be a multiple of 32");
-  static_assert(TW <= NT && TH <= NT, "halo passes need one thread per halo site");
-  static_assert(BBW <= NT, "tile bits are written by one thread each");
+  static_assert(TH % 32 == 0 && TH % H == 0, "TH must be a multiple of 32 and of H");
+  static_assert(NT % 32 == 0, "whole warps per tile");
+  static_assert(TW * TH <= 32768, "16-bit parents with a mark bit");
+  static_assert(MS < 32768, "slots fit below the mark bit");
 };
 
 struct TilePos {
@@ -220,39 +274,89 @@ __device__ __forceinline__ bool border_site(const TilePos& p, int j, int& y, int
   return x < p.ncols;
 }
 
-// Tile-local union-find over word-local runs. e_int / d_int exclude bonds
-// leaving the tile. s_eint holds e_int of every row-word of the tile.
-template <int WPR, int TH>
-__device__ __forceinline__ void tile_unions(int* par, uint32_t R, uint32_t e_int, uint32_t d_int,
-                                            uint32_t vmask, int ry, int w, int nrows,
-                                            const uint32_t (*s_eint)[WPR], int lbase, int* err) {
+// Valid bits of word w in a tile with ncols valid columns. Every shift in
+// these kernels keeps its count inside [0, 31]: an out-of-range shift is
+// undefined behaviour, and the optimiser has been seen to act on it even
+// behind a guarding conditional.
+__device__ __forceinline__ uint32_t word_mask(int ncols, int w) {
+  const int nb = max(0, min(32, ncols - 32 * w));
+  return nb == 0 ? 0u : (0xffffffffu >> (32 - nb));
+}
+
+// Bit of the tile's last valid column inside word w (0 if w does not hold it).
+__device__ __forceinline__ uint32_t last_column_bit(int ncols, int w) {
+  const int pl = ncols - 1 - 32 * w;
+  return (pl >= 0 && pl < 32) ? (1u << (pl & 31)) : 0u;
+}
+
+// The tile-local clusters of one thread's strip: parents of its sites set
+// to themselves, then the rows scanned top to bottom. e_int/d_int hold the
+// strip's east and south bonds that stay inside the tile.
+template <int WPR, int H>
+__device__ __forceinline__ void strip_scan(uint16_t* par, const uint32_t (&e_int)[H], const uint32_t (&d_int)[H],
+                                           uint32_t vmask, int y0r, int nv, int w) {
   constexpr int TW = 32 * WPR;
-  if ((e_int >> 31) & 1u) unite_local(par, lbase + run_start(R, 31), lbase + 32, err);
-  if (d_int && ry + 1 < nrows) {
-    const uint32_t eb = s_eint[ry + 1][w];
-    const uint32_t Rb = ~(eb << 1) & vmask;
-    // an S bond at b is redundant when b-1 has one too and b-1,b share a run in both rows
-    uint32_t need = d_int & ~((d_int & e_int & eb) << 1);
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    const int base = (y0r + r) * TW + 32 * w;
+    uint4* p4 = reinterpret_cast<uint4*>(par + base);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t b = (uint32_t)(base + 8 * q);
+      p4[q] = make_uint4(b | ((b + 1) << 16), (b + 2) | ((b + 3) << 16), (b + 4) | ((b + 5) << 16),
+                         (b + 6) | ((b + 7) << 16));
+    }
+  }
+#pragma unroll
+  for (int r = 1; r < H; ++r) {
+    if (r >= nv) break;
+    const uint32_t ep = e_int[r - 1], ec = e_int[r], du = d_int[r - 1];
+    const uint32_t Rp = ~(ep << 1) & vmask, Rc = ~(ec << 1) & vmask;
+    // a south bond at j is redundant when j-1 has one and j-1,j share a run in both rows
+    uint32_t need = du & ~((du & ep & ec) << 1);
+    const int bp = (y0r + r - 1) * TW + 32 * w, bc = bp + TW;
     while (need) {
-      const int b = __ffs(need) - 1;
+      const int j = __ffs(need) - 1;
       need &= need - 1;
-      unite_local(par, lbase + run_start(R, b), lbase + TW + run_start(Rb, b), err);
+      const int ra = find_own(par, bp + run_start(Rp, j));
+      const int B = bc + run_start(Rc, j);
+      const int pb = par[B];
+      if (pb == B) {
+        par[B] = (uint16_t)ra;  // first link of run B: ra < B
+      } else {
+        const int rb = find_own(par, pb);
+        if (ra < rb) par[rb] = (uint16_t)ra;
+        else if (rb < ra) par[ra] = (uint16_t)rb;
+      }
     }
   }
 }
 
-__device__ __forceinline__ void compress_runs(int* par, uint32_t R, int lbase) {
-  while (R) {
-    const int b = __ffs(R) - 1;
-    R &= R - 1;
-    par[lbase + b] = find_local(par, lbase + b);
+// Bonds leaving a strip: south bonds into its first row from the strip
+// above, and east bonds from each word into the next one. Atomic unions.
+template <int WPR, int TH, int H>
+__device__ __forceinline__ void strip_joins(uint16_t* par, const uint32_t (&e_int)[H], uint32_t vmask, int y0r,
+                                            int nv, int w, const uint32_t (*s_eint)[WPR],
+                                            const uint32_t (*s_dint)[WPR], int* err) {
+  constexpr int TW = 32 * WPR;
+  if (y0r > 0 && nv > 0) {
+    const uint32_t ep = s_eint[y0r - 1][w], du = s_dint[y0r - 1][w], ec = e_int[0];
+    const uint32_t Rp = ~(ep << 1) & vmask, Rc = ~(ec << 1) & vmask;
+    uint32_t need = du & ~((du & ep & ec) << 1);
+    const int bp = (y0r - 1) * TW + 32 * w, bc = bp + TW;
+    while (need) {
+      const int j = __ffs(need) - 1;
+      need &= need - 1;
+      unite_shared(par, bp + run_start(Rp, j), bc + run_start(Rc, j), err);
+    }
   }
-}
-
-__device__ __forceinline__ void init_parents(int* par, int lbase) {
-  int4* p4 = reinterpret_cast<int4*>(par + lbase);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) p4[k] = make_int4(lbase + 4 * k, lbase + 4 * k + 1, lbase + 4 * k + 2, lbase + 4 * k + 3);
+  for (int r = 0; r < H; ++r) {
+    if (r < nv && ((e_int[r] >> 31) & 1u)) {
+      const int base = (y0r + r) * TW + 32 * w;
+      unite_shared(par, base + run_start(~(e_int[r] << 1), 31), base + 32, err);
+    }
+  }
 }
 
 template <typename T>
@@ -264,156 +368,257 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 __device__ __forceinline__ int log2_floor(uint32_t v) { return 31 - __clz(v); }
 
+// Exclusive prefix sums of popc(mask[i]), i < RW, into pre[i]; returns the
+// total. Words are split into contiguous chunks of C per thread. Called by
+// every thread of the block (contains barriers).
+template <int RW, int NT>
+__device__ __forceinline__ int block_popc_prefix(const uint32_t* mask, uint32_t* pre, uint32_t* s_wsum) {
+  constexpr int C = (RW + NT - 1) / NT;
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t loc[C];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int i = tid * C + c;
+    loc[c] = sum;
+    sum += i < RW ? (uint32_t)__popc(mask[i]) : 0u;
+  }
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t v = lane < NW ? s_wsum[lane] : 0u;
+    uint32_t in2 = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, in2, o);
+      if (lane >= o) in2 += t;
+    }
+    __syncwarp();
+    if (lane < NW) s_wsum[lane] = in2 - v;
+    if (lane == 31) s_wsum[32] = in2;
+  }
+  __syncthreads();
+  const uint32_t base = s_wsum[warp] + incl - sum;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int i = tid * C + c;
+    if (i < RW) pre[i] = base + loc[c];
+  }
+  const int total = (int)s_wsum[32];
+  __syncthreads();
+  return total;
+}
+
+// Slot of border root r: its rank among the marked roots in index order.
+__device__ __forceinline__ int slot_of(const uint32_t* bmask, const uint32_t* pre, int r) {
+  return (int)(pre[r >> 5] + (uint32_t)__popc(bmask[r >> 5] & ((1u << (r & 31)) - 1u)));
+}
+
 // ================================================================ phase 1
 
-template <int WPR, int TH>
-__global__ void __launch_bounds__(WPR * TH) phase1_kernel(const SweepArgs a) {
-  using T = Tile<WPR, TH>;
-  constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW;
-  __shared__ __align__(16) int par[TH * TW];
+template <int WPR, int TH, int H>
+__global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs a) {
+  using T = Tile<WPR, TH, H>;
+  constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
+  __shared__ __align__(16) uint16_t par[TH * TW];
   __shared__ uint32_t s_spin[TH][WPR];
   __shared__ uint32_t s_eint[TH][WPR];
+  __shared__ uint32_t s_dint[TH][WPR];
   __shared__ uint32_t s_bb[BBW];
   __shared__ int s_broot[NB];
-  __shared__ int s_nslots;
+  __shared__ uint32_t s_bmask[RW];   // border roots
+  __shared__ uint32_t s_pre[RW];     // prefix counts of s_bmask
+  __shared__ uint32_t s_wsum[33];
 
   const Geometry& g = a.g;
   const int L = g.L;
   const TilePos P = tile_pos<TW, TH>(g, blockIdx.x);
-  const int tid = threadIdx.x, ry = tid / WPR, w = tid % WPR;
+  const int tid = threadIdx.x, w = tid % WPR, k = tid / WPR, y0r = k * H;
+  const int lane = tid & 31, warp0 = tid & ~31;
+  const int nv = max(0, min(H, P.nrows - y0r));  // valid rows of my strip
   uint32_t* eout = s_bb + T::OFF_EOUT;
   uint32_t* sout = s_bb + T::OFF_SOUT;
   uint32_t* hE = s_bb + T::OFF_HE;
   uint32_t* hS = s_bb + T::OFF_HS;
 
-  if (tid < BBW) s_bb[tid] = 0u;
-  if (tid == 0) s_nslots = 0;
+  for (int i = tid; i < BBW; i += NT) s_bb[i] = 0u;
+  for (int i = tid; i < RW; i += NT) s_bmask[i] = 0u;
 
-  // ---- spins of my word
+  // ---- spins of my strip
   const int nb = max(0, min(32, P.ncols - 32 * w));
-  const bool rowv = ry < P.nrows;
-  const uint32_t vmask = (!rowv || nb == 0) ? 0u : (nb == 32 ? 0xffffffffu : ((1u << nb) - 1u));
-  uint32_t s = 0;
-  if (vmask) s = load_spin_bits(a.spins_in + (size_t)(P.y0 + ry) * L + P.x0 + 32 * w, nb, g.aligned16);
-  s_spin[ry][w] = s;
+  const uint32_t wmask = word_mask(P.ncols, w);
+  uint32_t s[H];
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    s[r] = 0u;
+    if (r < nv && wmask)
+      s[r] = load_spin_bits(a.spins_in + (size_t)(P.y0 + y0r + r) * L + P.x0 + 32 * w, nb, g.aligned16);
+    s_spin[y0r + r][w] = s[r];
+  }
   __syncthreads();
 
   // ---- east halo column and south halo row (periodic wrap)
   const int xe = (P.x0 + P.ncols) % L;
   const int ys = (P.y0 + P.nrows) % L;
-  if (tid < TH) {
-    const bool bit = tid < P.nrows && a.spins_in[(size_t)(P.y0 + tid) * L + xe] < 0;
+  for (int b0 = warp0; b0 < TH; b0 += NT) {
+    const int y = b0 + lane;
+    const bool bit = y < P.nrows && a.spins_in[(size_t)(P.y0 + y) * L + xe] < 0;
     const uint32_t m = __ballot_sync(0xffffffffu, bit);
-    if ((tid & 31) == 0) hE[tid >> 5] = m;
+    if (lane == 0) hE[b0 >> 5] = m;
   }
-  if (tid < WPR) {
-    const int nbw = max(0, min(32, P.ncols - 32 * tid));
-    hS[tid] = nbw ? load_spin_bits(a.spins_in + (size_t)ys * L + P.x0 + 32 * tid, nbw, g.aligned16) : 0u;
+  for (int ww = tid; ww < WPR; ww += NT) {
+    const int nbw = max(0, min(32, P.ncols - 32 * ww));
+    hS[ww] = nbw ? load_spin_bits(a.spins_in + (size_t)ys * L + P.x0 + 32 * ww, nbw, g.aligned16) : 0u;
   }
   __syncthreads();
 
   // ---- bonds (§2.1)
-  const bool lastword = nb > 0 && 32 * (w + 1) >= P.ncols;  // holds the tile's last column
-  const int pl = P.ncols - 1 - 32 * w;                       // that column's bit
-  uint32_t sE;
-  if (lastword) {
-    const uint32_t hb = (hE[ry >> 5] >> (ry & 31)) & 1u;
-    sE = ((s >> 1) & ((1u << pl) - 1u)) | (hb << pl);
-  } else {
-    sE = (s >> 1) | ((w + 1 < WPR) ? (s_spin[ry][w + 1] << 31) : 0u);
-  }
-  const uint32_t sS = (ry + 1 < P.nrows) ? s_spin[ry + 1][w] : hS[w];
-  const uint32_t eqE = ~(s ^ sE) & vmask, eqS = ~(s ^ sS) & vmask;
-
-  uint32_t rE = 0, rS = 0;
-  if (vmask) {
-    const uint32_t i0 = (uint32_t)(P.y0 + ry) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w);
-    if ((L & 1) == 0) {
-      // even L: sites i0+b, i0+b+1 (b even) share Philox block (i0+b)/2
+  const uint32_t lbit = last_column_bit(P.ncols, w);  // nonzero iff my word holds the tile's last column
+  const bool lastword = lbit != 0u;
+  uint32_t e_int[H], d_int[H];
+  uint32_t* tb = a.tb.tbits + (size_t)P.tile * 3 * RW;
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    const int y = y0r + r;
+    const uint32_t vmask = r < nv ? wmask : 0u;
+    uint32_t sE;
+    if (lastword) {
+      const uint32_t hb = (hE[y >> 5] >> (y & 31)) & 1u;
+      sE = ((s[r] >> 1) & (lbit - 1u)) | (hb ? lbit : 0u);
+    } else {
+      sE = (s[r] >> 1) | ((w + 1 < WPR) ? (s_spin[y][w + 1] << 31) : 0u);
+    }
+    const uint32_t sS = (y + 1 < P.nrows) ? (r + 1 < H ? s[r + 1] : s_spin[y + 1][w]) : hS[w];
+    const uint32_t eqE = ~(s[r] ^ sE) & vmask, eqS = ~(s[r] ^ sS) & vmask;
+    uint32_t rE = 0, rS = 0;
+    if (vmask) {
+      const uint32_t i0 = (uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w);
+      if ((L & 1) == 0) {
+        // even L: sites i0+b, i0+b+1 (b even) share Philox block (i0+b)/2
 #pragma unroll 4
-      for (int b = 0; b < 32; b += 2) {
-        if (b < nb) {
-          const uint4 r = philox4x32_10(make_uint4((i0 + b) >> 1, a.t, 0u, 0u), a.ks);
-          rE |= ((uint32_t)(r.x < a.thr) << b) | ((uint32_t)(r.z < a.thr) << (b + 1));
-          rS |= ((uint32_t)(r.y < a.thr) << b) | ((uint32_t)(r.w < a.thr) << (b + 1));
+        for (int b = 0; b < 32; b += 2) {
+          if (b < nb) {
+            const uint4 q = philox4x32_10(make_uint4((i0 + b) >> 1, a.t, 0u, 0u), a.ks);
+            rE |= ((uint32_t)(q.x < a.thr) << b) | ((uint32_t)(q.z < a.thr) << (b + 1));
+            rS |= ((uint32_t)(q.y < a.thr) << b) | ((uint32_t)(q.w < a.thr) << (b + 1));
+          }
+        }
+      } else {
+        for (int b = 0; b < nb; ++b) {
+          const uint32_t i = i0 + b;
+          const uint4 q = philox4x32_10(make_uint4(i >> 1, a.t, 0u, 0u), a.ks);
+          const uint32_t we = (i & 1u) ? q.z : q.x, ws = (i & 1u) ? q.w : q.y;
+          rE |= (uint32_t)(we < a.thr) << b;
+          rS |= (uint32_t)(ws < a.thr) << b;
         }
       }
-    } else {
-      for (int b = 0; b < nb; ++b) {
-        const uint32_t i = i0 + b;
-        const uint4 r = philox4x32_10(make_uint4(i >> 1, a.t, 0u, 0u), a.ks);
-        const uint32_t we = (i & 1u) ? r.z : r.x, ws = (i & 1u) ? r.w : r.y;
-        rE |= (uint32_t)(we < a.thr) << b;
-        rS |= (uint32_t)(ws < a.thr) << b;
-      }
     }
-  }
-  const uint32_t e = eqE & rE, d = eqS & rS;
-  const uint32_t e_int = lastword ? (e & ~(1u << pl)) : e;
-  const uint32_t d_int = (ry + 1 < P.nrows) ? d : 0u;
-  s_eint[ry][w] = e_int;
-  if (lastword && ((e >> pl) & 1u)) atomicOr(&eout[ry >> 5], 1u << (ry & 31));
-  if (rowv && ry == P.nrows - 1) sout[w] = d;
-  {
-    uint32_t* tb = a.tb.tbits + (size_t)P.tile * 3 * NT;
-    tb[tid] = s;
-    tb[NT + tid] = e;
-    tb[2 * NT + tid] = d;
+    const uint32_t e = eqE & rE, d = eqS & rS;
+    e_int[r] = e & ~lbit;
+    d_int[r] = (y + 1 < P.nrows) ? d : 0u;
+    s_eint[y][w] = e_int[r];
+    s_dint[y][w] = d_int[r];
+    if (r < nv && (e & lbit)) atomicOr(&eout[y >> 5], 1u << (y & 31));
+    if (r < nv && y == P.nrows - 1) sout[w] = d;
+    const int rw = y * WPR + w;
+    tb[rw] = s[r];
+    tb[RW + rw] = e;
+    tb[2 * RW + rw] = d;
   }
 
   // ---- tile-local clusters (§2.3)
-  const int lbase = ry * TW + 32 * w;
-  init_parents(par, lbase);
+  strip_scan<WPR, H>(par, e_int, d_int, wmask, y0r, nv, w);
   __syncthreads();
-  const uint32_t R = ~(e_int << 1) & vmask;
-  tile_unions<WPR, TH>(par, R, e_int, d_int, vmask, ry, w, P.nrows, s_eint, lbase, a.tb.err);
-  __syncthreads();
-  compress_runs(par, R, lbase);
+  strip_joins<WPR, TH, H>(par, e_int, wmask, y0r, nv, w, s_eint, s_dint, a.tb.err);
   __syncthreads();
 
-  // ---- border components -> slots and global nodes
+  // every run start of my strip points at its tile root
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    if (r >= nv) break;
+    const int base = (y0r + r) * TW + 32 * w;
+    uint32_t R = ~(e_int[r] << 1) & wmask;
+    while (R) {
+      const int b = __ffs(R) - 1;
+      R &= R - 1;
+      par[base + b] = (uint16_t)find_final(par, base + b);
+    }
+  }
+  __syncthreads();
+
+  // ---- border components -> slots (rank of the root in index order) and global nodes
   for (int j = tid; j < NB; j += NT) {
     int y, x, r = -1;
     if (border_site<TW, TH>(P, j, y, x)) {
-      const int rs = run_start(~(s_eint[y][x >> 5] << 1), x & 31);
-      r = par[y * TW + (x & ~31) + rs];
+      r = par[y * TW + (x & ~31) + run_start(~(s_eint[y][x >> 5] << 1), x & 31)];
+      atomicOr(&s_bmask[r >> 5], 1u << (r & 31));
     }
     s_broot[j] = r;
   }
   __syncthreads();
-  for (int j = tid; j < NB; j += NT) {
-    const int r = s_broot[j];
-    if (r >= 0 && atomicCAS(&par[r], r, kFlagClaim) == r) {
-      const int slot = atomicAdd(&s_nslots, 1);
-      par[r] = kFlagClaim | slot;
-      const uint32_t node = (uint32_t)P.tile * MS + (uint32_t)slot;
-      const uint32_t key = (uint32_t)(P.y0 + r / TW) * (uint32_t)L + (uint32_t)(P.x0 + r % TW);
-      a.tb.nodes[node] = ((uint64_t)key << 32) | node;
-      if (a.csize) a.csize[node] = 0u;
+  const int nsl = block_popc_prefix<RW, NT>(s_bmask, s_pre, s_wsum);
+  {
+    constexpr int C = (RW + NT - 1) / NT;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int i = tid * C + c;
+      if (i >= RW) break;
+      uint32_t m = s_bmask[i];
+      uint32_t slot = s_pre[i];
+      while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        const int r = i * 32 + b;
+        const uint32_t node = (uint32_t)P.tile * MS + slot;
+        const uint32_t key = (uint32_t)(P.y0 + r / TW) * (uint32_t)L + (uint32_t)(P.x0 + r % TW);
+        a.tb.nodes[node] = ((uint64_t)key << 32) | node;
+        if (a.csize) a.csize[node] = 0u;
+        ++slot;
+      }
     }
   }
-  __syncthreads();
   uint16_t* bs = a.tb.bslot + (size_t)P.tile * NB;
   for (int j = tid; j < NB; j += NT) {
     const int r = s_broot[j];
-    bs[j] = r >= 0 ? (uint16_t)(par[r] & ~kFlagClaim) : (uint16_t)0xFFFFu;
+    bs[j] = r >= 0 ? (uint16_t)slot_of(s_bmask, s_pre, r) : (uint16_t)0xFFFFu;
   }
-  if (tid < BBW) a.tb.bbits[(size_t)P.tile * BBW + tid] = s_bb[tid];
+  // roots and border marks of my strip for phase 3
+  {
+    uint16_t* rt = a.tb.roots + (size_t)P.tile * (TW * TH);
+    uint32_t* bm = a.tb.bmask + (size_t)P.tile * RW;
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+      const int base = (y0r + r) * TW + 32 * w;
+      const uint4* src = reinterpret_cast<const uint4*>(par + base);
+      uint4* dst = reinterpret_cast<uint4*>(rt + base);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = src[q];
+      bm[(y0r + r) * WPR + w] = s_bmask[(y0r + r) * WPR + w];
+    }
+  }
+  for (int i = tid; i < BBW; i += NT) a.tb.bbits[(size_t)P.tile * BBW + i] = s_bb[i];
   if (tid == 0) {
-    if (s_nslots > MS) atomicCAS(a.tb.err, 0, kErrSlotOverflow);
-    a.tb.nslots[P.tile] = s_nslots;
+    if (nsl > MS) atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+    a.tb.nslots[P.tile] = nsl;
   }
   if (P.tile == 0) {
     if (a.em && tid < 2) a.em[tid] = 0;
-    if (a.hist && tid < 34) a.hist[tid] = 0;
+    for (int i = tid; a.hist && i < 34; i += NT) a.hist[i] = 0;
   }
 }
 
 // ================================================================ phase 2
 
-template <int WPR, int TH>
+template <int WPR, int TH, int H>
 __global__ void phase2_kernel(const SweepArgs a) {
-  using T = Tile<WPR, TH>;
+  using T = Tile<WPR, TH, H>;
   constexpr int TW = T::TW, NB = T::NB, MS = T::MS, BBW = T::BBW;
   const Geometry& g = a.g;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -432,6 +637,10 @@ __global__ void phase2_kernel(const SweepArgs a) {
     const int tileE = P.ty * g.tiles_x + (P.tx + 1) % g.tiles_x;
     const uint16_t* bsE = a.tb.bslot + (size_t)tileE * NB;
     const uint16_t sa = bs[TH + y], sb = bsE[y];
+    if (sa >= a.tb.nslots[tile] || sb >= a.tb.nslots[tileE]) {
+      atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+      return;
+    }
     if (y > 0 && ((eo[(y - 1) >> 5] >> ((y - 1) & 31)) & 1u) && bs[TH + y - 1] == sa && bsE[y - 1] == sb) return;
     unite_global(a.tb.nodes, (uint32_t)tile * MS + sa, (uint32_t)tileE * MS + sb, a.tb.err);
   } else {
@@ -442,6 +651,10 @@ __global__ void phase2_kernel(const SweepArgs a) {
     const int tileS = ((P.ty + 1) % g.tiles_y) * g.tiles_x + P.tx;
     const uint16_t* bsS = a.tb.bslot + (size_t)tileS * NB;
     const uint16_t sa = bs[2 * TH + TW + x], sb = bsS[2 * TH + x];
+    if (sa >= a.tb.nslots[tile] || sb >= a.tb.nslots[tileS]) {
+      atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+      return;
+    }
     if (x > 0 && ((so[(x - 1) >> 5] >> ((x - 1) & 31)) & 1u) && bs[2 * TH + TW + x - 1] == sa &&
         bsS[2 * TH + x - 1] == sb)
       return;
@@ -452,17 +665,18 @@ __global__ void phase2_kernel(const SweepArgs a) {
 // ================================================================ phase 3
 
 // MODE 0: flips + E/M; 1: flips + E/M + cluster sizes; 2: canonical labels.
-template <int WPR, int TH, int MODE>
-__global__ void __launch_bounds__(WPR * TH) phase3_kernel(const SweepArgs a) {
-  using T = Tile<WPR, TH>;
-  constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW;
+template <int WPR, int TH, int H, int MODE>
+__global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs a) {
+  using T = Tile<WPR, TH, H>;
+  constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
   constexpr bool HIST = MODE == 1, LABELS = MODE == 2;
-  __shared__ __align__(16) int par[TH * TW];
-  __shared__ uint32_t s_eint[TH][WPR];
+  __shared__ __align__(16) uint16_t par[TH * TW];  // tile root of every run start (from phase 1)
+  __shared__ uint32_t s_bmask[RW];                 // border roots
+  __shared__ uint32_t s_pre[RW];
+  __shared__ uint32_t s_wsum[33];
+  __shared__ uint32_t s_flip[RW];                  // flip bit of every root
   __shared__ uint32_t s_snew[TH][WPR];
-  __shared__ uint32_t s_iflip[NT];       // flip bit of inner roots, one word per thread
-  __shared__ int s_broot[NB];
-  __shared__ int s_slotval[MS];          // flip bit (flip modes) or canonical label (labels mode)
+  __shared__ int s_slotval[MS];                    // flip bit (flip modes) or canonical label (labels mode)
   __shared__ uint32_t s_slotroot[HIST ? MS : 1];
   __shared__ uint32_t s_hEnew[TH / 32], s_hSnew[TW / 32];
   __shared__ long long s_red[2][NT / 32];
@@ -472,34 +686,41 @@ __global__ void __launch_bounds__(WPR * TH) phase3_kernel(const SweepArgs a) {
   const Geometry& g = a.g;
   const int L = g.L;
   const TilePos P = tile_pos<TW, TH>(g, blockIdx.x);
-  const int tid = threadIdx.x, ry = tid / WPR, w = tid % WPR;
-
-  const uint32_t* tb = a.tb.tbits + (size_t)P.tile * 3 * NT;
-  const uint32_t s = tb[tid], e = tb[NT + tid], d = tb[2 * NT + tid];
+  const int tid = threadIdx.x, w = tid % WPR, k = tid / WPR, y0r = k * H;
+  const int lane = tid & 31, warp0 = tid & ~31;
+  const int nv = max(0, min(H, P.nrows - y0r));
   const int nb = max(0, min(32, P.ncols - 32 * w));
-  const bool rowv = ry < P.nrows;
-  const uint32_t vmask = (!rowv || nb == 0) ? 0u : (nb == 32 ? 0xffffffffu : ((1u << nb) - 1u));
-  const bool lastword = nb > 0 && 32 * (w + 1) >= P.ncols;
-  const int pl = P.ncols - 1 - 32 * w;
-  const uint32_t e_int = lastword ? (e & ~(1u << pl)) : e;
-  const uint32_t d_int = (ry + 1 < P.nrows) ? d : 0u;
-  s_eint[ry][w] = e_int;
-  const int lbase = ry * TW + 32 * w;
-  init_parents(par, lbase);
-  if (HIST) {
-    int4* z = reinterpret_cast<int4*>(s_size + lbase);
+  const uint32_t wmask = word_mask(P.ncols, w);
+  const uint32_t lbit = last_column_bit(P.ncols, w);
+  const bool lastword = lbit != 0u;
+
+  const uint32_t* tb = a.tb.tbits + (size_t)P.tile * 3 * RW;
+  const uint16_t* groots = a.tb.roots + (size_t)P.tile * (TW * TH);
+  const uint32_t* gbm = a.tb.bmask + (size_t)P.tile * RW;
+  uint32_t s[H], e_int[H];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) z[k] = make_int4(0, 0, 0, 0);
-    if (tid < 34) s_hist[tid] = 0ull;
+  for (int r = 0; r < H; ++r) {
+    const int y = y0r + r, rw = y * WPR + w, base = y * TW + 32 * w;
+    s[r] = tb[rw];
+    e_int[r] = tb[RW + rw] & ~lbit;
+    s_bmask[rw] = gbm[rw];
+    const uint4* src = reinterpret_cast<const uint4*>(groots + base);
+    uint4* dst = reinterpret_cast<uint4*>(par + base);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = src[q];
+    if (HIST) {
+      int4* z = reinterpret_cast<int4*>(s_size + base);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) z[q] = make_int4(0, 0, 0, 0);
+    }
   }
+  if (HIST)
+    for (int i = tid; i < 34; i += NT) s_hist[i] = 0ull;
   __syncthreads();
-  const uint32_t R = ~(e_int << 1) & vmask;
-  tile_unions<WPR, TH>(par, R, e_int, d_int, vmask, ry, w, P.nrows, s_eint, lbase, a.tb.err);
-  __syncthreads();
-  compress_runs(par, R, lbase);
+  const int nsl = a.tb.nslots[P.tile];
+  if (block_popc_prefix<RW, NT>(s_bmask, s_pre, s_wsum) != nsl && tid == 0) atomicCAS(a.tb.err, 0, kErrSlotOverflow);
 
   // ---- global roots of this tile's slots
-  const int nsl = a.tb.nslots[P.tile];
   for (int j = tid; j < nsl; j += NT) {
     const uint64_t v = find_global(a.tb.nodes, (uint32_t)P.tile * MS + j, a.tb.err);
     const uint32_t key = (uint32_t)(v >> 32);
@@ -507,171 +728,198 @@ __global__ void __launch_bounds__(WPR * TH) phase3_kernel(const SweepArgs a) {
     if (HIST) s_slotroot[j] = (uint32_t)v;
   }
   __syncthreads();
-  for (int j = tid; j < NB; j += NT) {
-    int y, x, r = -1;
-    if (border_site<TW, TH>(P, j, y, x)) {
-      const int rs = run_start(~(s_eint[y][x >> 5] << 1), x & 31);
-      r = par[y * TW + (x & ~31) + rs];
-    }
-    s_broot[j] = r;
-  }
-  __syncthreads();
-  // border roots: par[r] = -1 - slot
-  const uint16_t* bs = a.tb.bslot + (size_t)P.tile * NB;
-  for (int j = tid; j < NB; j += NT) {
-    const int r = s_broot[j];
-    if (r >= 0) par[r] = -1 - (int)bs[j];
-  }
-  __syncthreads();
-  // inner roots of my word: their flip bits (one Philox block per root)
+
+  // ---- flip bit of every root of my strip: border roots from their slot,
+  // inner roots from one Philox block each (C6)
   if (!LABELS) {
-    uint32_t fl = 0, RR = R;
-    while (RR) {
-      const int b = __ffs(RR) - 1;
-      RR &= RR - 1;
-      const int l = lbase + b;
-      if (par[l] == l) {
-        const uint32_t key = (uint32_t)(P.y0 + ry) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w + b);
-        fl |= flip_bit(key, a.t, a.ks) << b;
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+      const int y = y0r + r, base = y * TW + 32 * w, rw = y * WPR + w;
+      uint32_t fl = 0;
+      if (r < nv) {
+        uint32_t R = ~(e_int[r] << 1) & wmask;
+        const uint32_t bm = s_bmask[rw];
+        while (R) {
+          const int b = __ffs(R) - 1;
+          R &= R - 1;
+          if (par[base + b] != base + b) continue;
+          uint32_t f;
+          if ((bm >> b) & 1u) {
+            const int sl = slot_of(s_bmask, s_pre, base + b);
+            f = sl < nsl ? (uint32_t)s_slotval[sl] : 0u;
+          } else {
+            f = flip_bit((uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w + b), a.t, a.ks);
+          }
+          fl |= f << b;
+        }
       }
+      s_flip[rw] = fl;
     }
-    s_iflip[tid] = fl;
     __syncthreads();
   }
 
-  // ---- per run: root and its decision
-  uint32_t tmask = 0, fprev = 0;
-  {
-    uint32_t RR = R;
-    while (RR) {
-      const int b = __ffs(RR) - 1;
-      RR &= RR - 1;
-      const int l = lbase + b;
-      int r = l, p = par[l];
-      if (p >= 0 && p != l) {
-        r = p;
-        p = par[r];
-      }
-      // p < 0: border root with slot -1-p; p == r: inner root r
+  // ---- per run: its root's decision; new spins of my strip
+  uint32_t snew[H];
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    snew[r] = s[r];
+    if (r >= nv || !wmask) continue;
+    const int y = y0r + r, base = y * TW + 32 * w;
+    uint32_t R = ~(e_int[r] << 1) & wmask;
+    uint32_t tmask = 0, fprev = 0;
+    while (R) {
+      const int b = __ffs(R) - 1;
+      R &= R - 1;
+      const int rt = par[base + b];
       if (LABELS) {
-        const int nxt = RR ? (__ffs(RR) - 1) : nb;
-        const int key = p < 0 ? s_slotval[-1 - p]
-                              : (int)((uint32_t)(P.y0 + r / TW) * (uint32_t)L + (uint32_t)(P.x0 + r % TW));
-        int32_t* out = a.labels + (size_t)(P.y0 + ry) * L + P.x0 + 32 * w;
+        const int nxt = R ? (__ffs(R) - 1) : nb;
+        int key;
+        if ((s_bmask[rt >> 5] >> (rt & 31)) & 1u) {
+          const int sl = slot_of(s_bmask, s_pre, rt);
+          key = sl < nsl ? s_slotval[sl] : 0;
+        } else {
+          key = (int)((uint32_t)(P.y0 + rt / TW) * (uint32_t)L + (uint32_t)(P.x0 + rt % TW));
+        }
+        int32_t* out = a.labels + (size_t)(P.y0 + y) * L + P.x0 + 32 * w;
         for (int x = b; x < nxt; ++x) out[x] = key;
       } else {
-        const uint32_t f = p < 0 ? (uint32_t)s_slotval[-1 - p] : ((s_iflip[r >> 5] >> (r & 31)) & 1u);
+        const uint32_t f = (s_flip[rt >> 5] >> (rt & 31)) & 1u;
         tmask |= (f ^ fprev) << b;
         fprev = f;
         if (HIST) {
-          const int nxt = RR ? (__ffs(RR) - 1) : nb;
-          atomicAdd(&s_size[r], nxt - b);
+          const int nxt = R ? (__ffs(R) - 1) : nb;
+          atomicAdd(&s_size[rt], nxt - b);
         }
       }
     }
+    if (!LABELS) {
+      // prefix xor turns "decision changes at this run start" into per-site flips
+      tmask ^= tmask << 1;
+      tmask ^= tmask << 2;
+      tmask ^= tmask << 4;
+      tmask ^= tmask << 8;
+      tmask ^= tmask << 16;
+      snew[r] = s[r] ^ (tmask & wmask);
+      store_spin_bits(a.spins_out + (size_t)(P.y0 + y) * L + P.x0 + 32 * w, snew[r], nb, g.aligned16);
+    }
   }
   if (LABELS) return;
-
-  // prefix xor turns "decision changes at this run start" into per-site flips
-  tmask ^= tmask << 1;
-  tmask ^= tmask << 2;
-  tmask ^= tmask << 4;
-  tmask ^= tmask << 8;
-  tmask ^= tmask << 16;
-  const uint32_t snew = s ^ (tmask & vmask);
-  if (vmask) store_spin_bits(a.spins_out + (size_t)(P.y0 + ry) * L + P.x0 + 32 * w, snew, nb, g.aligned16);
-  s_snew[ry][w] = snew;
+#pragma unroll
+  for (int r = 0; r < H; ++r) s_snew[y0r + r][w] = snew[r];
 
   // ---- new spins of the halo sites: old spin (phase 1) xor their cluster's flip
   const uint32_t* bbits = a.tb.bbits + (size_t)P.tile * BBW;
-  if (tid < TH) {
+  for (int b0 = warp0; b0 < TH; b0 += NT) {
+    const int y = b0 + lane;
     bool bit = false;
-    if (tid < P.nrows) {
+    if (y < P.nrows) {
       const int tileE = P.ty * g.tiles_x + (P.tx + 1) % g.tiles_x;
-      const uint16_t slot = a.tb.bslot[(size_t)tileE * NB + tid];
+      uint16_t slot = a.tb.bslot[(size_t)tileE * NB + y];
+      if (slot >= MS) {
+        atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+        slot = 0;
+      }
       const uint64_t v = find_global(a.tb.nodes, (uint32_t)tileE * MS + slot, a.tb.err);
-      const uint32_t old = (bbits[T::OFF_HE + (tid >> 5)] >> (tid & 31)) & 1u;
+      const uint32_t old = (bbits[T::OFF_HE + (y >> 5)] >> (y & 31)) & 1u;
       bit = (old ^ flip_bit((uint32_t)(v >> 32), a.t, a.ks)) != 0u;
     }
     const uint32_t m = __ballot_sync(0xffffffffu, bit);
-    if ((tid & 31) == 0) s_hEnew[tid >> 5] = m;
+    if (lane == 0) s_hEnew[b0 >> 5] = m;
   }
-  if (tid < TW) {
+  for (int b0 = warp0; b0 < TW; b0 += NT) {
+    const int x = b0 + lane;
     bool bit = false;
-    if (tid < P.ncols) {
+    if (x < P.ncols) {
       const int tileS = ((P.ty + 1) % g.tiles_y) * g.tiles_x + P.tx;
-      const uint16_t slot = a.tb.bslot[(size_t)tileS * NB + 2 * TH + tid];
+      uint16_t slot = a.tb.bslot[(size_t)tileS * NB + 2 * TH + x];
+      if (slot >= MS) {
+        atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+        slot = 0;
+      }
       const uint64_t v = find_global(a.tb.nodes, (uint32_t)tileS * MS + slot, a.tb.err);
-      const uint32_t old = (bbits[T::OFF_HS + (tid >> 5)] >> (tid & 31)) & 1u;
+      const uint32_t old = (bbits[T::OFF_HS + (x >> 5)] >> (x & 31)) & 1u;
       bit = (old ^ flip_bit((uint32_t)(v >> 32), a.t, a.ks)) != 0u;
     }
     const uint32_t m = __ballot_sync(0xffffffffu, bit);
-    if ((tid & 31) == 0) s_hSnew[tid >> 5] = m;
+    if (lane == 0) s_hSnew[b0 >> 5] = m;
   }
   __syncthreads();
 
   // ---- E and M of the new state (C10)
-  uint32_t sEn;
-  if (lastword) {
-    const uint32_t hb = (s_hEnew[ry >> 5] >> (ry & 31)) & 1u;
-    sEn = ((snew >> 1) & ((1u << pl) - 1u)) | (hb << pl);
-  } else {
-    sEn = (snew >> 1) | ((w + 1 < WPR) ? (s_snew[ry][w + 1] << 31) : 0u);
+  int eloc = 0, mloc = 0;
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    if (r >= nv || !wmask) continue;
+    const int y = y0r + r;
+    uint32_t sEn;
+    if (lastword) {
+      const uint32_t hb = (s_hEnew[y >> 5] >> (y & 31)) & 1u;
+      sEn = ((snew[r] >> 1) & (lbit - 1u)) | (hb ? lbit : 0u);
+    } else {
+      sEn = (snew[r] >> 1) | ((w + 1 < WPR) ? (s_snew[y][w + 1] << 31) : 0u);
+    }
+    const uint32_t sSn = (y + 1 < P.nrows) ? (r + 1 < H ? snew[r + 1] : s_snew[y + 1][w]) : s_hSnew[w];
+    const int nvb = __popc(wmask);
+    const int unequal = __popc((snew[r] ^ sEn) & wmask) + __popc((snew[r] ^ sSn) & wmask);
+    eloc += 2 * unequal - 2 * nvb;
+    mloc += nvb - 2 * __popc(snew[r] & wmask);
   }
-  const uint32_t sSn = (ry + 1 < P.nrows) ? s_snew[ry + 1][w] : s_hSnew[w];
-  const int nv = __popc(vmask);
-  const int unequal = __popc((snew ^ sEn) & vmask) + __popc((snew ^ sSn) & vmask);
-  long long eloc = 2LL * unequal - 2LL * nv;
-  long long mloc = (long long)nv - 2LL * __popc(snew & vmask);
-  eloc = warp_sum(eloc);
-  mloc = warp_sum(mloc);
-  if ((tid & 31) == 0) {
-    s_red[0][tid >> 5] = eloc;
-    s_red[1][tid >> 5] = mloc;
+  long long ev = warp_sum((long long)eloc), mv = warp_sum((long long)mloc);
+  if (lane == 0) {
+    s_red[0][tid >> 5] = ev;
+    s_red[1][tid >> 5] = mv;
   }
 
   if (HIST) {
     // sizes are complete after this barrier: bin inner clusters here, send
     // border pieces to their global root
     __syncthreads();
-    uint32_t RR = R;
-    while (RR) {
-      const int b = __ffs(RR) - 1;
-      RR &= RR - 1;
-      const int l = lbase + b;
-      const int p = par[l];
-      if (p == l) {
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+      if (r >= nv) break;
+      const int base = (y0r + r) * TW + 32 * w, rw = (y0r + r) * WPR + w;
+      uint32_t R = ~(e_int[r] << 1) & wmask;
+      while (R) {
+        const int b = __ffs(R) - 1;
+        R &= R - 1;
+        const int l = base + b;
+        if (par[l] != l) continue;
         const uint32_t sz = (uint32_t)s_size[l];
-        atomicAdd(&s_hist[0], 1ull);
-        atomicAdd(&s_hist[1], (unsigned long long)sz * sz);
-        atomicAdd(&s_hist[2 + log2_floor(sz)], 1ull);
-      } else if (p < 0) {
-        atomicAdd(&a.csize[s_slotroot[-1 - p]], (uint32_t)s_size[l]);
+        if ((s_bmask[rw] >> b) & 1u) {
+          const int sl = slot_of(s_bmask, s_pre, l);
+          if (sl < nsl) atomicAdd(&a.csize[s_slotroot[sl]], sz);
+        } else {
+          atomicAdd(&s_hist[0], 1ull);
+          atomicAdd(&s_hist[1], (unsigned long long)sz * sz);
+          atomicAdd(&s_hist[2 + log2_floor(sz)], 1ull);
+        }
       }
     }
   }
   __syncthreads();
   if (tid < 32) {
-    long long ev = 0, mv = 0;
-    for (int k = tid; k < NT / 32; k += 32) {
-      ev += s_red[0][k];
-      mv += s_red[1][k];
+    long long e2 = 0, m2 = 0;
+    for (int q = tid; q < NT / 32; q += 32) {
+      e2 += s_red[0][q];
+      m2 += s_red[1][q];
     }
-    ev = warp_sum(ev);
-    mv = warp_sum(mv);
+    e2 = warp_sum(e2);
+    m2 = warp_sum(m2);
     if (tid == 0) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(a.em), (unsigned long long)ev);
-      atomicAdd(reinterpret_cast<unsigned long long*>(a.em + 1), (unsigned long long)mv);
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.em), (unsigned long long)e2);
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.em + 1), (unsigned long long)m2);
     }
   }
-  if (HIST && tid < 34 && s_hist[tid]) atomicAdd(reinterpret_cast<unsigned long long*>(a.hist + tid), s_hist[tid]);
+  if (HIST)
+    for (int i = tid; i < 34; i += NT)
+      if (s_hist[i]) atomicAdd(reinterpret_cast<unsigned long long*>(a.hist + i), s_hist[i]);
 }
 
 // ================================================================ phase 4
 
-template <int WPR, int TH>
+template <int WPR, int TH, int H>
 __global__ void phase4_kernel(const SweepArgs a) {
-  using T = Tile<WPR, TH>;
+  using T = Tile<WPR, TH, H>;
   constexpr int MS = T::MS;
   __shared__ unsigned long long s_hist[34];
   if (threadIdx.x < 34) s_hist[threadIdx.x] = 0ull;
@@ -712,18 +960,18 @@ __global__ void check_spins_kernel(const int8_t* spins, long long n, int* err) {
   }
 }
 
-template <int WPR, int TH>
+template <int WPR, int TH, int H>
 __global__ void export_bonds_kernel(const SweepArgs a, uint8_t* out) {
-  constexpr int TW = 32 * WPR, NT = WPR * TH;
+  constexpr int TW = 32 * WPR, RW = WPR * TH;
   const int L = a.g.L;
   const long long n = (long long)L * L;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(i / L), x = (int)(i % L);
     const int tile = (y / TH) * a.g.tiles_x + x / TW;
     const int ry = y % TH, xx = x % TW;
-    const int t = ry * WPR + (xx >> 5), b = xx & 31;
-    const uint32_t* tb = a.tb.tbits + (size_t)tile * 3 * NT;
-    out[i] = (uint8_t)(((tb[NT + t] >> b) & 1u) | (((tb[2 * NT + t] >> b) & 1u) << 1));
+    const int rw = ry * WPR + (xx >> 5), b = xx & 31;
+    const uint32_t* tb = a.tb.tbits + (size_t)tile * 3 * RW;
+    out[i] = (uint8_t)(((tb[RW + rw] >> b) & 1u) | (((tb[2 * RW + rw] >> b) & 1u) << 1));
   }
 }
 
@@ -733,53 +981,63 @@ int grid_for(long long n, int block) {
   return (int)(g < 1 ? 1 : g);
 }
 
-template <int WPR, int TH>
+template <int WPR, int TH, int H>
 cudaError_t launch_all(int which, const SweepArgs& a, int mode, uint8_t* out, cudaStream_t st) {
-  using T = Tile<WPR, TH>;
+  using T = Tile<WPR, TH, H>;
   const int ntiles = a.g.tiles_x * a.g.tiles_y;
   switch (which) {
     case 1:
-      phase1_kernel<WPR, TH><<<ntiles, T::NT, 0, st>>>(a);
+      phase1_kernel<WPR, TH, H><<<ntiles, T::NT, 0, st>>>(a);
       break;
     case 2: {
       const long long total = (long long)ntiles * (TH + T::TW);
-      phase2_kernel<WPR, TH><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
+      phase2_kernel<WPR, TH, H><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
       break;
     }
     case 3:
       if (mode == 0) {
-        phase3_kernel<WPR, TH, 0><<<ntiles, T::NT, 0, st>>>(a);
+        phase3_kernel<WPR, TH, H, 0><<<ntiles, T::NT, 0, st>>>(a);
       } else if (mode == 1) {
         const size_t dyn = (size_t)TH * T::TW * sizeof(int);
         static bool attr_done = false;
         if (!attr_done) {
-          cudaError_t e = cudaFuncSetAttribute(phase3_kernel<WPR, TH, 1>,
+          cudaError_t e = cudaFuncSetAttribute(phase3_kernel<WPR, TH, H, 1>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
           if (e != cudaSuccess) return e;
           attr_done = true;
         }
-        phase3_kernel<WPR, TH, 1><<<ntiles, T::NT, dyn, st>>>(a);
+        phase3_kernel<WPR, TH, H, 1><<<ntiles, T::NT, dyn, st>>>(a);
       } else {
-        phase3_kernel<WPR, TH, 2><<<ntiles, T::NT, 0, st>>>(a);
+        phase3_kernel<WPR, TH, H, 2><<<ntiles, T::NT, 0, st>>>(a);
       }
       break;
     case 4: {
       const long long total = (long long)ntiles * T::MS;
-      phase4_kernel<WPR, TH><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
+      phase4_kernel<WPR, TH, H><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
       break;
     }
     case 5:
-      export_bonds_kernel<WPR, TH><<<grid_for((long long)a.g.L * a.g.L, 256), 256, 0, st>>>(a, out);
+      export_bonds_kernel<WPR, TH, H><<<grid_for((long long)a.g.L * a.g.L, 256), 256, 0, st>>>(a, out);
       break;
   }
   return cudaGetLastError();
 }
 
+template <int V>
+cudaError_t launch_shape(int which, const SweepArgs& a, int mode, uint8_t* out, cudaStream_t st) {
+  constexpr TileShape ts = shape_of(V);
+  return launch_all<ts.wpr, ts.th, ts.h>(which, a, mode, out, st);
+}
+
 cudaError_t dispatch(int shape, int which, const SweepArgs& a, int mode, uint8_t* out, cudaStream_t st) {
   switch (shape) {
-    case 0: return launch_all<4, 64>(which, a, mode, out, st);
-    case 1: return launch_all<4, 32>(which, a, mode, out, st);
-    case 2: return launch_all<2, 64>(which, a, mode, out, st);
+    case 0: return launch_shape<0>(which, a, mode, out, st);
+    case 1: return launch_shape<1>(which, a, mode, out, st);
+    case 2: return launch_shape<2>(which, a, mode, out, st);
+    case 3: return launch_shape<3>(which, a, mode, out, st);
+    case 4: return launch_shape<4>(which, a, mode, out, st);
+    case 5: return launch_shape<5>(which, a, mode, out, st);
+    case 6: return launch_shape<6>(which, a, mode, out, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -11,7 +11,7 @@
 // file-scope device array instead of from allocations.
 //
 // The array is a static __device__ object, so every GPU that loads the
-// library holds it (kNoallocScratchBytes, under 1 MiB) until the process
+// library holds it (kNoallocScratchBytes, under 4 MiB) until the process
 // exits. Its name in host code is only a host-side stand-in for the device
 // object; the device address is obtained once per device with
 // cudaGetSymbolAddress and passed to the kernels.
@@ -26,14 +26,15 @@
 
 namespace {
 
-constexpr int kNoallocShape = 0;  // 128 x 64 tiles, as sw_sweep uses for L > 64
+constexpr int kNoallocShape = 6;  // 128 x 64 tiles, 2-row strips, as sw_sweep uses for L > 64
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct ScratchLayout {
-  size_t tbits, nodes, bslot, bbits, nslots, total;
+  size_t tbits, roots, bmask, nodes, bslot, bbits, nslots, total;
 };
 
-// Buffer sizes of the tile pipeline (as sw_create allocates them) for side L.
+// Buffer sizes of the tile pipeline (as sw_create allocates them) for side L;
+// `threads` counts row-words (one 32-bit word per row per word column).
 constexpr ScratchLayout layout_for(int L) {
   constexpr int th = sw::shape_of(kNoallocShape).th;
   constexpr int tw = 32 * sw::shape_of(kNoallocShape).wpr;
@@ -44,7 +45,9 @@ constexpr ScratchLayout layout_for(int L) {
   const size_t ntiles = (size_t)((L + tw - 1) / tw) * (size_t)((L + th - 1) / th);
   ScratchLayout s{};
   s.tbits = 0;
-  s.nodes = s.tbits + align256(ntiles * 3 * threads * sizeof(uint32_t));
+  s.roots = s.tbits + align256(ntiles * 3 * threads * sizeof(uint32_t));
+  s.bmask = s.roots + align256(ntiles * (size_t)tw * th * sizeof(uint16_t));
+  s.nodes = s.bmask + align256(ntiles * threads * sizeof(uint32_t));
   s.bslot = s.nodes + align256(ntiles * slots * sizeof(uint64_t));
   s.bbits = s.bslot + align256(ntiles * border * sizeof(uint16_t));
   s.nslots = s.bbits + align256(ntiles * bbits * sizeof(uint32_t));
@@ -101,7 +104,7 @@ extern "C" int sw_sweep_noalloc(int8_t* spins, int32_t L, double beta, uint64_t 
   cudaStream_t st = (cudaStream_t)stream;
   const ScratchLayout lay = layout_for(L);
   const sw::TileShape ts = sw::shape_of(kNoallocShape);
-  static_assert(layout_for(SW_NOALLOC_MAX_L).total < (1u << 20), "scratch must stay under 1 MiB");
+  static_assert(layout_for(SW_NOALLOC_MAX_L).total < (4u << 20), "scratch must stay under 4 MiB");
 
   sw::SweepArgs a{};
   a.g.L = L;
@@ -111,6 +114,8 @@ extern "C" int sw_sweep_noalloc(int8_t* spins, int32_t L, double beta, uint64_t 
   a.thr = threshold_for(beta);
   a.ks = sw::make_key_schedule(seed);
   a.tb.tbits = reinterpret_cast<uint32_t*>(base + lay.tbits);
+  a.tb.roots = reinterpret_cast<uint16_t*>(base + lay.roots);
+  a.tb.bmask = reinterpret_cast<uint32_t*>(base + lay.bmask);
   a.tb.nodes = reinterpret_cast<uint64_t*>(base + lay.nodes);
   a.tb.bslot = reinterpret_cast<uint16_t*>(base + lay.bslot);
   a.tb.bbits = reinterpret_cast<uint32_t*>(base + lay.bbits);
