@@ -183,6 +183,68 @@ int sw_timing(sw_lattice* h, int32_t enable);
  * NULL. */
 int sw_timing_read(sw_lattice* h, double* ms_out, int64_t* launches_out);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent lattices (replicas) of any sides and
+ * temperatures advanced together. The paper runs one lattice at a time; this
+ * applies its sweep (§2) to every replica at once, each replica following
+ * exactly the chain it would follow alone (same conventions C1-C10, keyed by
+ * its own seed and counter), so results are bit-identical to sw_sweep.
+ * Every phase of a sweep is one launch over the tiles of all replicas; an
+ * n-sweep sequence is captured as a CUDA graph and replayed while the
+ * membership and n stay the same. Replicas may be added and removed between
+ * sw_batch_sweep calls (continuous batching).
+ * --------------------------------------------------------------------------- */
+typedef struct sw_batch sw_batch;
+
+/* Create a batch with n >= 0 replicas (side L[i], beta[i], seed[i], init[i]
+ * or SW_INIT_HOT when init is NULL). shape: a compiled tile shape index or
+ * -1 for the default. stream: as for sw_create. The batch owns all device
+ * memory of its replicas. Errors: SW_EINVAL, SW_ENOMEM, SW_ECUDA. */
+int sw_batch_create(int32_t n, const int32_t* L, const double* beta, const uint64_t* seed,
+                    const int32_t* init, int32_t shape, void* stream, sw_batch** out);
+
+/* Add one replica; *slot_out receives its slot (stable until removed; freed
+ * slots are reused). Its sweep counter starts at 0. */
+int sw_batch_add(sw_batch* b, int32_t L, double beta, uint64_t seed, int32_t init, int32_t* slot_out);
+
+/* Remove the replica in `slot` (synchronises the stream, frees its memory). */
+int sw_batch_remove(sw_batch* b, int32_t slot);
+
+/* Advance every replica by n >= 0 sweeps, asynchronously on the batch's
+ * stream. Errors: SW_EINVAL, SW_ENOMEM (trace growth), SW_ECUDA. */
+int sw_batch_sweep(sw_batch* b, int32_t n);
+
+/* Let the replica in `slot` run only sweeps_left more sweeps (from its
+ * current counter); later sw_batch_sweep calls leave it idle once they are
+ * done, so it stops exactly at its target while the others go on. A
+ * negative value removes the limit. */
+int sw_batch_set_limit(sw_batch* b, int32_t slot, int64_t sweeps_left);
+
+/* Sweep counter of the replica in `slot`. */
+int sw_batch_get_sweep(sw_batch* b, int32_t slot, uint32_t* t_out);
+
+/* E and M of the replica's sweeps [first, first+count) (absolute counters,
+ * since its creation), as sw_observables. Synchronises; checks the error
+ * flag. */
+int sw_batch_observables(sw_batch* b, int32_t slot, int64_t first, int64_t count,
+                         int64_t* E_host, int64_t* M_host);
+
+/* Current spins of the replica, int8 [L][L], host (synchronises) or device. */
+int sw_batch_spins(sw_batch* b, int32_t slot, int8_t* out, int32_t out_is_device);
+
+/* Number of active replicas, their total sites and the device bytes they
+ * hold (any pointer may be NULL). */
+int sw_batch_info(sw_batch* b, int32_t* n_active, int64_t* sites, int64_t* device_bytes);
+
+/* Device bytes that sw_batch_add of a replica of side L, run for `sweeps`
+ * sweeps under a limit, makes this batch hold (spins, tile buffers and E/M
+ * trace, as requested from the allocator): the figure a server admits
+ * requests against its memory budget by. */
+int sw_batch_footprint(sw_batch* b, int32_t L, int64_t sweeps, int64_t* bytes);
+
+/* Release the batch and all its replicas. NULL is a no-op. */
+int sw_batch_destroy(sw_batch* b);
+
 /* Largest side accepted by sw_sweep_noalloc. */
 #define SW_NOALLOC_MAX_L 1024
 
@@ -213,6 +275,24 @@ int sw_timing_read(sw_lattice* h, double* ms_out, int64_t* launches_out);
  * launch failures SW_ECUDA. Calls no cudaMalloc/cudaFree. */
 int sw_sweep_noalloc(int8_t* spins, int32_t L, double beta, uint64_t seed, uint32_t t0, int32_t n,
                      int64_t* em, int32_t* err, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Tile shapes (measurement and tuning support; the paper fixes 32-wide tiles,
+ * §5). A sweep runs over tiles of tile_w x tile_h sites, each thread scanning
+ * a strip of strip_h rows of one 32-site word column.
+ * --------------------------------------------------------------------------- */
+
+/* Number of tile shapes compiled into the library (indices 0 .. n-1). */
+int sw_num_shapes(void);
+
+/* Geometry of a compiled tile shape (any output pointer may be NULL). */
+int sw_shape_info(int32_t shape, int32_t* tile_w, int32_t* tile_h, int32_t* strip_h, int32_t* threads);
+
+/* Process-wide preference: lattices whose side L has ceil(log2 L) ==
+ * log2_bucket (0..16) use `shape` from now on in sw_create, and batches
+ * created with shape -1 use the entry of their largest L; shape -1 restores
+ * the built-in default. Results never depend on the shape. */
+int sw_tune_shape(int32_t log2_bucket, int32_t shape);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* sw_last_error(void);

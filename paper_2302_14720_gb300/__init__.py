@@ -51,8 +51,23 @@ SIGNATURES = {
     "sw_bonds": (ctypes.c_int, [_P, _P]),
     "sw_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sw_timing_read": (ctypes.c_int, [_P, _P, _P]),
+    "sw_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(_P)]),
+    "sw_batch_add": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32)]),
+    "sw_batch_remove": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sw_batch_sweep": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sw_batch_footprint": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "sw_batch_set_limit": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
+    "sw_batch_get_sweep": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32)]),
+    "sw_batch_observables": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "sw_batch_spins": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "sw_batch_info": (ctypes.c_int, [_P, _P, _P, _P]),
+    "sw_batch_destroy": (ctypes.c_int, [_P]),
     "sw_sweep_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                                         ctypes.c_int32, _P, _P, _P]),
+    "sw_num_shapes": (ctypes.c_int, []),
+    "sw_shape_info": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P]),
+    "sw_tune_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
     "sw_last_error": (ctypes.c_char_p, []),
 }
 SW_NOALLOC_MAX_L = 1024
@@ -191,8 +206,96 @@ def sw_sweep_noalloc(spins_dev: int, L: int, beta: float, seed: int, t0: int, n:
                                  ctypes.c_void_p(stream) if stream else None), "sw_sweep_noalloc")
 
 
+def sw_num_shapes() -> int:
+    return int(_lib.sw_num_shapes())
+
+
+def sw_shape_info(shape: int) -> dict:
+    v = np.zeros(4, np.int32)
+    ptrs = [ctypes.c_void_p(v.ctypes.data + 4 * i) for i in range(4)]
+    _check(_lib.sw_shape_info(int(shape), *ptrs), "sw_shape_info")
+    return dict(tile_w=int(v[0]), tile_h=int(v[1]), strip_h=int(v[2]), threads=int(v[3]))
+
+
+def sw_tune_shape(log2_bucket: int, shape: int) -> None:
+    _check(_lib.sw_tune_shape(int(log2_bucket), int(shape)), "sw_tune_shape")
+
+
 def sw_last_error() -> str:
     return _lib.sw_last_error().decode()
+
+
+# ------------------------------------------------------------------ batch
+
+def sw_batch_create(L, beta, seed, init=None, shape: int = -1, stream: int | None = None) -> int:
+    n = len(L)
+    Ls = np.ascontiguousarray(L, dtype=np.int32)
+    bs = np.ascontiguousarray(beta, dtype=np.float64)
+    ss = np.ascontiguousarray(np.asarray(seed, dtype=np.uint64))
+    ins = None if init is None else np.ascontiguousarray(init, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(_lib.sw_batch_create(n, _host_ptr(Ls) if n else None, _host_ptr(bs) if n else None,
+                                _host_ptr(ss) if n else None, _host_ptr(ins) if ins is not None and n else None,
+                                int(shape), ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)),
+           "sw_batch_create")
+    return h.value
+
+
+def sw_batch_add(b: int, L: int, beta: float, seed: int, init: int = SW_INIT_HOT) -> int:
+    slot = ctypes.c_int32()
+    _check(_lib.sw_batch_add(b, int(L), float(beta), int(seed) & 0xFFFFFFFFFFFFFFFF, int(init), ctypes.byref(slot)),
+           "sw_batch_add")
+    return slot.value
+
+
+def sw_batch_remove(b: int, slot: int) -> None:
+    _check(_lib.sw_batch_remove(b, int(slot)), "sw_batch_remove")
+
+
+def sw_batch_sweep(b: int, n: int) -> None:
+    _check(_lib.sw_batch_sweep(b, int(n)), "sw_batch_sweep")
+
+
+def sw_batch_set_limit(b: int, slot: int, sweeps_left: int) -> None:
+    _check(_lib.sw_batch_set_limit(b, int(slot), int(sweeps_left)), "sw_batch_set_limit")
+
+
+def sw_batch_get_sweep(b: int, slot: int) -> int:
+    t = ctypes.c_uint32()
+    _check(_lib.sw_batch_get_sweep(b, int(slot), ctypes.byref(t)), "sw_batch_get_sweep")
+    return t.value
+
+
+def sw_batch_observables(b: int, slot: int, first: int, count: int):
+    E = np.zeros(max(count, 0), np.int64)
+    M = np.zeros(max(count, 0), np.int64)
+    _check(_lib.sw_batch_observables(b, int(slot), int(first), int(count), _host_ptr(E), _host_ptr(M)),
+           "sw_batch_observables")
+    return E, M
+
+
+def sw_batch_spins(b: int, slot: int, L: int) -> np.ndarray:
+    out = np.zeros((L, L), np.int8)
+    _check(_lib.sw_batch_spins(b, int(slot), _host_ptr(out), 0), "sw_batch_spins")
+    return out
+
+
+def sw_batch_info(b: int):
+    n = np.zeros(1, np.int32)
+    sites = np.zeros(1, np.int64)
+    nbytes = np.zeros(1, np.int64)
+    _check(_lib.sw_batch_info(b, _host_ptr(n), _host_ptr(sites), _host_ptr(nbytes)), "sw_batch_info")
+    return int(n[0]), int(sites[0]), int(nbytes[0])
+
+
+def sw_batch_footprint(b: int, L: int, sweeps: int) -> int:
+    out = ctypes.c_int64(0)
+    _check(_lib.sw_batch_footprint(b, int(L), int(sweeps), ctypes.byref(out)), "sw_batch_footprint")
+    return out.value
+
+
+def sw_batch_destroy(b: int) -> None:
+    _check(_lib.sw_batch_destroy(b), "sw_batch_destroy")
 
 
 # ------------------------------------------------------------ convenience

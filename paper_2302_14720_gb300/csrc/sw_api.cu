@@ -7,7 +7,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <cstdarg>
+#include <mutex>
 #include <cstdio>
 #include <new>
 #include <string>
@@ -51,15 +53,34 @@ uint32_t threshold_of(double beta) {
   return (uint32_t)scaled;
 }
 
+constexpr int kBuckets = 17;  // ceil(log2 L) for 2 <= L <= 46340
+std::atomic<int> g_tuned[kBuckets];
+std::once_flag g_tuned_once;
+
+int bucket_of(int L) {
+  int b = 0;
+  while ((1 << b) < L) ++b;
+  return b < kBuckets ? b : kBuckets - 1;
+}
+
 int shape_for(int L) {
   if (const char* env = getenv("SW_TILE_SHAPE")) {
     const int v = atoi(env);
     if (v >= 0 && v < sw::kNumShapes) return v;
   }
+  std::call_once(g_tuned_once, [] {
+    for (auto& x : g_tuned) x.store(-1);
+  });
+  const int t = g_tuned[bucket_of(L)].load();
+  if (t >= 0) return t;
   return L <= 64 ? 2 : 6;
 }
 
 }  // namespace
+
+namespace sw {
+int default_shape(int L) { return shape_for(L); }
+}  // namespace sw
 
 namespace sw {
 int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -435,6 +456,26 @@ int sw_set_state(sw_lattice* h, const int8_t* spins, uint32_t t, int32_t in_is_d
   }
   h->t = t;
   h->t_base = t;
+  return SW_OK;
+}
+
+int sw_num_shapes(void) { return sw::kNumShapes; }
+
+int sw_shape_info(int32_t shape, int32_t* tile_w, int32_t* tile_h, int32_t* strip_h, int32_t* threads) {
+  if (shape < 0 || shape >= sw::kNumShapes) return fail(SW_EINVAL, "unknown tile shape %d", shape);
+  const sw::TileShape ts = sw::shape_of(shape);
+  if (tile_w) *tile_w = ts.tw();
+  if (tile_h) *tile_h = ts.th;
+  if (strip_h) *strip_h = ts.h;
+  if (threads) *threads = ts.threads();
+  return SW_OK;
+}
+
+int sw_tune_shape(int32_t log2_bucket, int32_t shape) {
+  if (log2_bucket < 0 || log2_bucket >= kBuckets) return fail(SW_EINVAL, "bucket must be in [0, %d)", kBuckets);
+  if (shape < -1 || shape >= sw::kNumShapes) return fail(SW_EINVAL, "unknown tile shape %d", shape);
+  shape_for(2);  // initialise the table
+  g_tuned[log2_bucket].store(shape);
   return SW_OK;
 }
 

@@ -24,6 +24,7 @@ struct TileShape {
   int wpr;  // 32-bit words per tile row
   int th;   // rows per tile
   int h;    // rows per thread strip
+  int pl;   // rounds of pairwise strip merging done without atomics
   int tw() const { return 32 * wpr; }
   int row_words() const { return wpr * th; }
   int sites() const { return tw() * th; }
@@ -34,15 +35,18 @@ struct TileShape {
 };
 
 // Shapes compiled into the library; index = variant id.
-constexpr int kNumShapes = 7;
+constexpr int kNumShapes = 10;
 __host__ __device__ constexpr TileShape shape_of(int v) {
-  return v == 0   ? TileShape{4, 64, 4}
-         : v == 1 ? TileShape{4, 64, 8}
-         : v == 2 ? TileShape{2, 64, 4}
-         : v == 3 ? TileShape{8, 64, 4}
-         : v == 4 ? TileShape{4, 128, 4}
-         : v == 5 ? TileShape{8, 64, 8}
-                  : TileShape{4, 64, 2};
+  return v == 0   ? TileShape{4, 64, 4, 0}
+         : v == 1 ? TileShape{4, 64, 8, 0}
+         : v == 2 ? TileShape{2, 64, 4, 0}
+         : v == 3 ? TileShape{8, 64, 4, 0}
+         : v == 4 ? TileShape{4, 128, 4, 0}
+         : v == 5 ? TileShape{8, 64, 8, 0}
+         : v == 6 ? TileShape{4, 64, 2, 0}
+         : v == 7 ? TileShape{4, 64, 2, 1}
+         : v == 8 ? TileShape{4, 64, 2, 2}
+                  : TileShape{4, 64, 2, 3};
 }
 
 // Per-lattice device buffers of the tile pipeline.
@@ -79,8 +83,32 @@ struct SweepArgs {
 
 inline int ntiles_of(const Geometry& g) { return g.tiles_x * g.tiles_y; }
 
+// One replica of a batch, resident on the device. `a` holds its geometry,
+// threshold, key schedule, buffers and spins; the sweep counter and the
+// trace position advance on the device, so one captured launch sequence can
+// be replayed for any number of sweeps.
+struct ReplicaDesc {
+  SweepArgs a;
+  int tile0;          // first tile of this replica in the batch's tile numbering
+  int active;         // 0: slot free (its tiles are not launched)
+  uint32_t t;         // counter of the next sweep (C8)
+  int64_t t_left;     // sweeps still to run (the replica idles at 0)
+  int64_t* em_base;   // E/M trace [cap][2]
+  int64_t em_next;    // trace row of the next sweep
+};
+
+struct BatchArgs {
+  ReplicaDesc* descs;
+  const int* tile_rep;  // batch tile -> replica index
+  int nrep;
+};
+
 // Set the thread's last error message (sw_last_error) and return code.
 int record_error(int code, const char* msg);
+
+// Tile shape for a lattice of side L: SW_TILE_SHAPE override, else the
+// tuned entry of L's size bucket, else the built-in default.
+int default_shape(int L);
 
 // Launchers (sw_kernels.cu). Each returns cudaGetLastError() of its launches.
 cudaError_t launch_init(int8_t* spins, int L, uint64_t seed, int cold, cudaStream_t st);
@@ -93,6 +121,10 @@ cudaError_t launch_phase2(int shape, const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_phase3(int shape, const SweepArgs& a, bool labels_mode, cudaStream_t st);
 // Phase 4 (statistics only): log2 histogram of cluster sizes held at global roots.
 cudaError_t launch_phase4(int shape, const SweepArgs& a, cudaStream_t st);
+// Batch: phase 1, 2 or 3 (which = 1..3) over `ntiles` tiles of all replicas.
+cudaError_t launch_batch_phase(int shape, int which, const BatchArgs& b, int ntiles, cudaStream_t st);
+// Batch: advance every active replica's sweep counter and trace row by one.
+cudaError_t launch_batch_advance(const BatchArgs& b, cudaStream_t st);
 // Debug: expand the stored bond bits into uint8 [L][L] (bit0 east, bit1 south).
 cudaError_t launch_export_bonds(int shape, const SweepArgs& a, uint8_t* out, cudaStream_t st);
 

@@ -334,12 +334,34 @@ __device__ __forceinline__ void strip_scan(uint16_t* par, const uint32_t (&e_int
 
 // Bonds leaving a strip: south bonds into its first row from the strip
 // above, and east bonds from each word into the next one. Atomic unions.
-template <int WPR, int TH, int H>
+template <int WPR, int TH, int H, int PL>
 __device__ __forceinline__ void strip_joins(uint16_t* par, const uint32_t (&e_int)[H], uint32_t vmask, int y0r,
-                                            int nv, int w, const uint32_t (*s_eint)[WPR],
+                                            int nv, int w, int k, const uint32_t (*s_eint)[WPR],
                                             const uint32_t (*s_dint)[WPR], int* err) {
   constexpr int TW = 32 * WPR;
-  if (y0r > 0 && nv > 0) {
+  // The first PL rounds merge strips pairwise without atomics: in round st
+  // the boundary above strip k is joined when k % (2 st) == st, by k's
+  // thread, which then alone touches the 2 st strips of the two groups (trees
+  // do not cross word columns yet). The other boundaries follow with atomics.
+#pragma unroll
+  for (int lv = 0; lv < PL; ++lv) {
+    const int st = 1 << lv;
+    if (k % (2 * st) == st && nv > 0) {
+      const uint32_t ep = s_eint[y0r - 1][w], du = s_dint[y0r - 1][w], ec = e_int[0];
+      const uint32_t Rp = ~(ep << 1) & vmask, Rc = ~(ec << 1) & vmask;
+      uint32_t need = du & ~((du & ep & ec) << 1);
+      const int bp = (y0r - 1) * TW + 32 * w, bc = bp + TW;
+      while (need) {
+        const int j = __ffs(need) - 1;
+        need &= need - 1;
+        const int ra = find_own(par, bp + run_start(Rp, j)), rb = find_own(par, bc + run_start(Rc, j));
+        if (ra < rb) par[rb] = (uint16_t)ra;
+        else if (rb < ra) par[ra] = (uint16_t)rb;
+      }
+    }
+    __syncthreads();
+  }
+  if (y0r > 0 && nv > 0 && (k % (1 << PL)) == 0) {
     const uint32_t ep = s_eint[y0r - 1][w], du = s_dint[y0r - 1][w], ec = e_int[0];
     const uint32_t Rp = ~(ep << 1) & vmask, Rc = ~(ec << 1) & vmask;
     uint32_t need = du & ~((du & ep & ec) << 1);
@@ -421,10 +443,30 @@ __device__ __forceinline__ int slot_of(const uint32_t* bmask, const uint32_t* pr
   return (int)(pre[r >> 5] + (uint32_t)__popc(bmask[r >> 5] & ((1u << (r & 31)) - 1u)));
 }
 
+// The sweep arguments of this CTA's tile: the kernel parameter for one
+// lattice, or the replica descriptor of the batch tile blockIdx.x.
+template <bool BATCH>
+__device__ __forceinline__ bool cta_args(const SweepArgs& a0, const BatchArgs& b, SweepArgs& A, int& tile) {
+  if (!BATCH) {
+    A = a0;
+    tile = blockIdx.x;
+    return true;
+  }
+  const int T = blockIdx.x;
+  const int r = b.tile_rep[T];
+  if (r < 0) return false;  // a spare tile of the launch bucket
+  const ReplicaDesc* D = b.descs + r;
+  A = D->a;
+  A.t = D->t;
+  A.em = D->em_base + 2 * D->em_next;
+  tile = T - D->tile0;
+  return D->active != 0 && D->t_left > 0;
+}
+
 // ================================================================ phase 1
 
-template <int WPR, int TH, int H>
-__global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs a) {
+template <int WPR, int TH, int H, int PL, bool BATCH>
+__global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs a0, const BatchArgs bat) {
   using T = Tile<WPR, TH, H>;
   constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
   __shared__ __align__(16) uint16_t par[TH * TW];
@@ -437,9 +479,12 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
   __shared__ uint32_t s_pre[RW];     // prefix counts of s_bmask
   __shared__ uint32_t s_wsum[33];
 
+  SweepArgs a;
+  int tile;
+  if (!cta_args<BATCH>(a0, bat, a, tile)) return;
   const Geometry& g = a.g;
   const int L = g.L;
-  const TilePos P = tile_pos<TW, TH>(g, blockIdx.x);
+  const TilePos P = tile_pos<TW, TH>(g, tile);
   const int tid = threadIdx.x, w = tid % WPR, k = tid / WPR, y0r = k * H;
   const int lane = tid & 31, warp0 = tid & ~31;
   const int nv = max(0, min(H, P.nrows - y0r));  // valid rows of my strip
@@ -536,7 +581,7 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
   // ---- tile-local clusters (§2.3)
   strip_scan<WPR, H>(par, e_int, d_int, wmask, y0r, nv, w);
   __syncthreads();
-  strip_joins<WPR, TH, H>(par, e_int, wmask, y0r, nv, w, s_eint, s_dint, a.tb.err);
+  strip_joins<WPR, TH, H, PL>(par, e_int, wmask, y0r, nv, w, k, s_eint, s_dint, a.tb.err);
   __syncthreads();
 
   // every run start of my strip points at its tile root
@@ -616,16 +661,17 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
 
 // ================================================================ phase 2
 
-template <int WPR, int TH, int H>
-__global__ void phase2_kernel(const SweepArgs a) {
+// One CTA per tile, one thread per out-going border edge: TH east edges (rows)
+// then TW south edges (columns).
+template <int WPR, int TH, int H, bool BATCH>
+__global__ void phase2_kernel(const SweepArgs a0, const BatchArgs bat) {
   using T = Tile<WPR, TH, H>;
   constexpr int TW = T::TW, NB = T::NB, MS = T::MS, BBW = T::BBW;
+  SweepArgs a;
+  int tile;
+  if (!cta_args<BATCH>(a0, bat, a, tile)) return;
   const Geometry& g = a.g;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)g.tiles_x * g.tiles_y * (TH + TW);
-  if (idx >= total) return;
-  const int tile = (int)(idx / (TH + TW));
-  const int k = (int)(idx % (TH + TW));
+  const int k = threadIdx.x;
   const TilePos P = tile_pos<TW, TH>(g, tile);
   const uint32_t* bb = a.tb.bbits + (size_t)tile * BBW;
   const uint16_t* bs = a.tb.bslot + (size_t)tile * NB;
@@ -643,7 +689,7 @@ __global__ void phase2_kernel(const SweepArgs a) {
     }
     if (y > 0 && ((eo[(y - 1) >> 5] >> ((y - 1) & 31)) & 1u) && bs[TH + y - 1] == sa && bsE[y - 1] == sb) return;
     unite_global(a.tb.nodes, (uint32_t)tile * MS + sa, (uint32_t)tileE * MS + sb, a.tb.err);
-  } else {
+  } else if (k < TH + TW) {
     const int x = k - TH;
     if (x >= P.ncols) return;
     const uint32_t* so = bb + T::OFF_SOUT;
@@ -665,8 +711,8 @@ __global__ void phase2_kernel(const SweepArgs a) {
 // ================================================================ phase 3
 
 // MODE 0: flips + E/M; 1: flips + E/M + cluster sizes; 2: canonical labels.
-template <int WPR, int TH, int H, int MODE>
-__global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs a) {
+template <int WPR, int TH, int H, int MODE, bool BATCH>
+__global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs a0, const BatchArgs bat) {
   using T = Tile<WPR, TH, H>;
   constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
   constexpr bool HIST = MODE == 1, LABELS = MODE == 2;
@@ -683,9 +729,12 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
   __shared__ unsigned long long s_hist[HIST ? 34 : 1];
   extern __shared__ __align__(16) int s_size[];  // HIST: [TH * TW]
 
+  SweepArgs a;
+  int tile;
+  if (!cta_args<BATCH>(a0, bat, a, tile)) return;
   const Geometry& g = a.g;
   const int L = g.L;
-  const TilePos P = tile_pos<TW, TH>(g, blockIdx.x);
+  const TilePos P = tile_pos<TW, TH>(g, tile);
   const int tid = threadIdx.x, w = tid % WPR, k = tid / WPR, y0r = k * H;
   const int lane = tid & 31, warp0 = tid & ~31;
   const int nv = max(0, min(H, P.nrows - y0r));
@@ -943,6 +992,18 @@ __global__ void phase4_kernel(const SweepArgs a) {
     atomicAdd(reinterpret_cast<unsigned long long*>(a.hist + threadIdx.x), s_hist[threadIdx.x]);
 }
 
+// ================================================================ batch
+
+__global__ void batch_advance_kernel(const BatchArgs b) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= b.nrep) return;
+  ReplicaDesc* D = b.descs + r;
+  if (!D->active || D->t_left <= 0) return;
+  D->t += 1;
+  D->em_next += 1;
+  D->t_left -= 1;
+}
+
 // ================================================================ helpers
 
 __global__ void init_kernel(int8_t* spins, long long n, KeySchedule ks, int cold) {
@@ -981,35 +1042,43 @@ int grid_for(long long n, int block) {
   return (int)(g < 1 ? 1 : g);
 }
 
-template <int WPR, int TH, int H>
-cudaError_t launch_all(int which, const SweepArgs& a, int mode, uint8_t* out, cudaStream_t st) {
+template <int WPR, int TH, int H, int PL>
+cudaError_t launch_all(int which, const SweepArgs& a, int mode, uint8_t* out, cudaStream_t st,
+                       const BatchArgs* batch, int batch_tiles) {
   using T = Tile<WPR, TH, H>;
-  const int ntiles = a.g.tiles_x * a.g.tiles_y;
+  const int ntiles = batch ? batch_tiles : a.g.tiles_x * a.g.tiles_y;
   switch (which) {
     case 1:
-      phase1_kernel<WPR, TH, H><<<ntiles, T::NT, 0, st>>>(a);
+      phase1_kernel<WPR, TH, H, PL, false><<<ntiles, T::NT, 0, st>>>(a, BatchArgs{});
       break;
-    case 2: {
-      const long long total = (long long)ntiles * (TH + T::TW);
-      phase2_kernel<WPR, TH, H><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
+    case 2:
+      phase2_kernel<WPR, TH, H, false><<<ntiles, TH + T::TW, 0, st>>>(a, BatchArgs{});
       break;
-    }
     case 3:
       if (mode == 0) {
-        phase3_kernel<WPR, TH, H, 0><<<ntiles, T::NT, 0, st>>>(a);
+        phase3_kernel<WPR, TH, H, 0, false><<<ntiles, T::NT, 0, st>>>(a, BatchArgs{});
       } else if (mode == 1) {
         const size_t dyn = (size_t)TH * T::TW * sizeof(int);
         static bool attr_done = false;
         if (!attr_done) {
-          cudaError_t e = cudaFuncSetAttribute(phase3_kernel<WPR, TH, H, 1>,
+          cudaError_t e = cudaFuncSetAttribute(phase3_kernel<WPR, TH, H, 1, false>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
           if (e != cudaSuccess) return e;
           attr_done = true;
         }
-        phase3_kernel<WPR, TH, H, 1><<<ntiles, T::NT, dyn, st>>>(a);
+        phase3_kernel<WPR, TH, H, 1, false><<<ntiles, T::NT, dyn, st>>>(a, BatchArgs{});
       } else {
-        phase3_kernel<WPR, TH, H, 2><<<ntiles, T::NT, 0, st>>>(a);
+        phase3_kernel<WPR, TH, H, 2, false><<<ntiles, T::NT, 0, st>>>(a, BatchArgs{});
       }
+      break;
+    case 11:
+      phase1_kernel<WPR, TH, H, PL, true><<<ntiles, T::NT, 0, st>>>(a, *batch);
+      break;
+    case 12:
+      phase2_kernel<WPR, TH, H, true><<<ntiles, TH + T::TW, 0, st>>>(a, *batch);
+      break;
+    case 13:
+      phase3_kernel<WPR, TH, H, 0, true><<<ntiles, T::NT, 0, st>>>(a, *batch);
       break;
     case 4: {
       const long long total = (long long)ntiles * T::MS;
@@ -1024,20 +1093,25 @@ cudaError_t launch_all(int which, const SweepArgs& a, int mode, uint8_t* out, cu
 }
 
 template <int V>
-cudaError_t launch_shape(int which, const SweepArgs& a, int mode, uint8_t* out, cudaStream_t st) {
+cudaError_t launch_shape(int which, const SweepArgs& a, int mode, uint8_t* out, cudaStream_t st,
+                         const BatchArgs* batch, int batch_tiles) {
   constexpr TileShape ts = shape_of(V);
-  return launch_all<ts.wpr, ts.th, ts.h>(which, a, mode, out, st);
+  return launch_all<ts.wpr, ts.th, ts.h, ts.pl>(which, a, mode, out, st, batch, batch_tiles);
 }
 
-cudaError_t dispatch(int shape, int which, const SweepArgs& a, int mode, uint8_t* out, cudaStream_t st) {
+cudaError_t dispatch(int shape, int which, const SweepArgs& a, int mode, uint8_t* out, cudaStream_t st,
+                     const BatchArgs* batch = nullptr, int batch_tiles = 0) {
   switch (shape) {
-    case 0: return launch_shape<0>(which, a, mode, out, st);
-    case 1: return launch_shape<1>(which, a, mode, out, st);
-    case 2: return launch_shape<2>(which, a, mode, out, st);
-    case 3: return launch_shape<3>(which, a, mode, out, st);
-    case 4: return launch_shape<4>(which, a, mode, out, st);
-    case 5: return launch_shape<5>(which, a, mode, out, st);
-    case 6: return launch_shape<6>(which, a, mode, out, st);
+    case 0: return launch_shape<0>(which, a, mode, out, st, batch, batch_tiles);
+    case 1: return launch_shape<1>(which, a, mode, out, st, batch, batch_tiles);
+    case 2: return launch_shape<2>(which, a, mode, out, st, batch, batch_tiles);
+    case 3: return launch_shape<3>(which, a, mode, out, st, batch, batch_tiles);
+    case 4: return launch_shape<4>(which, a, mode, out, st, batch, batch_tiles);
+    case 5: return launch_shape<5>(which, a, mode, out, st, batch, batch_tiles);
+    case 6: return launch_shape<6>(which, a, mode, out, st, batch, batch_tiles);
+    case 7: return launch_shape<7>(which, a, mode, out, st, batch, batch_tiles);
+    case 8: return launch_shape<8>(which, a, mode, out, st, batch, batch_tiles);
+    case 9: return launch_shape<9>(which, a, mode, out, st, batch, batch_tiles);
   }
   return cudaErrorInvalidValue;
 }
@@ -1063,6 +1137,18 @@ cudaError_t launch_phase3(int shape, const SweepArgs& a, bool labels_mode, cudaS
 cudaError_t launch_phase4(int shape, const SweepArgs& a, cudaStream_t st) { return dispatch(shape, 4, a, 0, nullptr, st); }
 cudaError_t launch_export_bonds(int shape, const SweepArgs& a, uint8_t* out, cudaStream_t st) {
   return dispatch(shape, 5, a, 0, out, st);
+}
+
+cudaError_t launch_batch_phase(int shape, int which, const BatchArgs& b, int ntiles, cudaStream_t st) {
+  if (which < 1 || which > 3) return cudaErrorInvalidValue;
+  if (ntiles <= 0) return cudaSuccess;
+  return dispatch(shape, 10 + which, SweepArgs{}, 0, nullptr, st, &b, ntiles);
+}
+
+cudaError_t launch_batch_advance(const BatchArgs& b, cudaStream_t st) {
+  if (b.nrep <= 0) return cudaSuccess;
+  batch_advance_kernel<<<(b.nrep + 127) / 128, 128, 0, st>>>(b);
+  return cudaGetLastError();
 }
 
 }  // namespace sw

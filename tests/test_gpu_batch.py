@@ -1,0 +1,135 @@
+"""Batched form (sw_batch_*): every replica of a batch must follow exactly
+the chain it follows alone -- same spins, E and M, bit for bit -- whatever
+the other replicas are, across graph re-captures, and while replicas join
+and leave between sweep calls (continuous batching)."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import batch_replicas
+
+pytestmark = pytest.mark.gpu
+
+BETA_C = 0.44068679
+
+
+@pytest.fixture(scope="module")
+def sw():
+    from conftest import build_libsw
+    build_libsw()
+    import paper_2302_14720_gb300 as sw
+    return sw
+
+
+def oracle_chain(L, beta, seed, n, cold=False):
+    s, E, M, _ = oracle.run(L, beta, seed, n, cold=cold)
+    return s, E, M
+
+
+@pytest.mark.parametrize("shape", [-1, 0, 6])
+def test_mixed_batch_matches_oracle(sw, shape):
+    reps = [(2, 0.3, 11, 0), (5, 0.6, 12, 1), (17, BETA_C, 13, 0), (64, 0.2, 14, 0),
+            (100, BETA_C, 15, 1), (128, 0.5, 16, 0), (257, 0.45, 17, 0), (64, BETA_C, 18, 0)]
+    L, beta, seed, init = (list(x) for x in zip(*reps))
+    b = sw.sw_batch_create(L, beta, seed, init, shape=shape)
+    try:
+        sw.sw_batch_sweep(b, 3)
+        sw.sw_batch_sweep(b, 4)   # a different n: the graph is captured again
+        sw.sw_batch_sweep(b, 3)   # same n as before: replay
+        for slot, (Lr, br, sr, ir) in enumerate(reps):
+            want_s, want_E, want_M = oracle_chain(Lr, br, sr, 10, cold=bool(ir))
+            assert sw.sw_batch_get_sweep(b, slot) == 10
+            assert np.array_equal(sw.sw_batch_spins(b, slot, Lr), want_s), slot
+            E, M = sw.sw_batch_observables(b, slot, 0, 10)
+            assert np.array_equal(E, want_E) and np.array_equal(M, want_M), slot
+    finally:
+        sw.sw_batch_destroy(b)
+
+
+def test_continuous_batching_join_and_leave(sw):
+    b = sw.sw_batch_create([33, 64, 80], [0.4, BETA_C, 0.55], [1, 2, 3])
+    try:
+        sw.sw_batch_sweep(b, 5)
+        s3 = sw.sw_batch_add(b, 48, 0.35, 4)
+        s4 = sw.sw_batch_add(b, 130, BETA_C, 5, sw.SW_INIT_COLD)
+        sw.sw_batch_sweep(b, 4)
+        sw.sw_batch_remove(b, 1)
+        sw.sw_batch_sweep(b, 3)
+        s5 = sw.sw_batch_add(b, 20, 0.8, 6)      # reuses the freed slot
+        assert s5 == 1
+        sw.sw_batch_sweep(b, 2)
+        n_active, sites, nbytes = sw.sw_batch_info(b)
+        assert n_active == 5 and sites == 33 * 33 + 80 * 80 + 48 * 48 + 130 * 130 + 20 * 20 and nbytes > sites
+        expect = {0: (33, 0.4, 1, 14, False), 2: (80, 0.55, 3, 14, False), s3: (48, 0.35, 4, 9, False),
+                  s4: (130, BETA_C, 5, 9, True), s5: (20, 0.8, 6, 2, False)}
+        for slot, (L, beta, seed, n, cold) in expect.items():
+            want_s, want_E, want_M = oracle_chain(L, beta, seed, n, cold)
+            assert sw.sw_batch_get_sweep(b, slot) == n
+            assert np.array_equal(sw.sw_batch_spins(b, slot, L), want_s), slot
+            E, M = sw.sw_batch_observables(b, slot, 0, n)
+            assert np.array_equal(E, want_E) and np.array_equal(M, want_M), slot
+        with pytest.raises(sw.SWError):
+            sw.sw_batch_spins(b, 7, 10)
+    finally:
+        sw.sw_batch_destroy(b)
+
+
+def test_batch_equals_solo_lattices_config_mix(sw):
+    # The 256-replica mix (L in {64..1024}, beta grid in [0.40, 0.48]); every
+    # 16th replica is compared with the same replica run alone with sw_sweep.
+    L, beta, seed = batch_replicas()
+    b = sw.sw_batch_create(L, beta, seed)
+    try:
+        sw.sw_batch_sweep(b, 4)
+        for slot in range(0, 256, 16):
+            with sw.Lattice(L[slot], beta[slot], seed[slot]) as lat:
+                lat.sweep(4)
+                assert np.array_equal(sw.sw_batch_spins(b, slot, L[slot]), lat.spins()), slot
+                Eb, Mb = sw.sw_batch_observables(b, slot, 0, 4)
+                E, M = lat.observables(0, 4)
+                assert np.array_equal(Eb, E) and np.array_equal(Mb, M), slot
+    finally:
+        sw.sw_batch_destroy(b)
+
+
+def test_empty_batch_and_errors(sw):
+    b = sw.sw_batch_create([], [], [])
+    try:
+        sw.sw_batch_sweep(b, 3)
+        assert sw.sw_batch_info(b)[0] == 0
+        with pytest.raises(sw.SWError) as ei:
+            sw.sw_batch_add(b, 1, 0.4, 1)
+        assert ei.value.status == sw.SW_EINVAL
+        with pytest.raises(sw.SWError):
+            sw.sw_batch_remove(b, 0)
+    finally:
+        sw.sw_batch_destroy(b)
+
+
+def test_sweep_limit_stops_each_replica_at_its_target(sw):
+    # Three replicas with targets 3, 7 and unlimited advance in chunks of 4:
+    # each stops exactly at its target, its chain equal to the oracle's,
+    # while the others go on; lifting a limit resumes the same chain.
+    reps = [(40, 0.5, 21, 3), (64, BETA_C, 22, 7), (33, 0.3, 23, None)]
+    b = sw.sw_batch_create([r[0] for r in reps], [r[1] for r in reps], [r[2] for r in reps])
+    try:
+        for slot, (_, _, _, target) in enumerate(reps):
+            if target is not None:
+                sw.sw_batch_set_limit(b, slot, target)
+        sw.sw_batch_sweep(b, 4)
+        sw.sw_batch_sweep(b, 4)
+        for slot, (L, beta, seed, target) in enumerate(reps):
+            n = 8 if target is None else target
+            assert sw.sw_batch_get_sweep(b, slot) == n
+            want_s, want_E, want_M = oracle_chain(L, beta, seed, n)
+            assert np.array_equal(sw.sw_batch_spins(b, slot, L), want_s), slot
+            E, M = sw.sw_batch_observables(b, slot, 0, n)
+            assert np.array_equal(E, want_E) and np.array_equal(M, want_M), slot
+        sw.sw_batch_set_limit(b, 0, -1)
+        sw.sw_batch_sweep(b, 4)
+        assert [sw.sw_batch_get_sweep(b, s) for s in range(3)] == [7, 7, 12]
+        want_s, want_E, _ = oracle_chain(40, 0.5, 21, 7)
+        assert np.array_equal(sw.sw_batch_spins(b, 0, 40), want_s)
+        assert np.array_equal(sw.sw_batch_observables(b, 0, 0, 7)[0], want_E)
+    finally:
+        sw.sw_batch_destroy(b)
