@@ -17,6 +17,10 @@ reports the whole-job rate.
 
 The reference arm (--impl reference) times the serial CPU oracle on the
 host cores on the same workload, one oracle sweep per step.
+
+Rank 0 also reports the 256-replica batch against the same replicas run one
+by one ("batched_vs_plain") and a bounded Poisson serving run through the
+continuous-batching server ("serving": p50/p99 latency, aggregate rate).
 """
 from __future__ import annotations
 
@@ -290,6 +294,14 @@ def run_ours(args):
 
     if rank != 0:
         return 0
+    batched = serving = None
+    if args.batched_sweeps > 0:
+        batched = measure_batched(sw, torch, stream, args.batched_sweeps, args.plain_sweeps)
+        log("batched:", json.dumps(batched))
+        if args.serving_requests > 0:
+            serving = measure_serving(sw, stream, args.serving_requests, batched["batched_su_s"],
+                                      args.serving_budget_gib)
+            log("serving:", json.dumps(serving))
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(args.cpu_sweeps, "sweeps")
@@ -310,9 +322,92 @@ def run_ours(args):
                 "steps": len(e2e_times), "ms_per_step": 1e3 * statistics.mean(e2e_times)},
         "gpu_launches": int(phase_n[:3].sum()),
         "clocks": clock_info,
+        "batched_vs_plain": batched,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_batched(sw, torch, stream, n_batched: int, n_plain: int):
+    """The 256-replica mix (L in {64..1024}, beta grid in [0.40, 0.48], hot
+    starts): one batched sweep over all replicas per graph node group versus
+    every replica swept alone on its own handle, one after the other."""
+    from workloads import batch_replicas
+    Ls, betas, seeds = batch_replicas()
+    sites = int(sum(int(x) * int(x) for x in Ls))
+    chunk = 50
+    b = sw.sw_batch_create(Ls, betas, seeds, stream=stream.cuda_stream)
+    try:
+        sw.sw_batch_sweep(b, chunk)             # warm-up: captures the graph
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_b = max(chunk, n_batched // chunk * chunk)
+        e0.record(stream)
+        for _ in range(n_b // chunk):
+            sw.sw_batch_sweep(b, chunk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_b = e0.elapsed_time(e1)
+        E, _ = sw.sw_batch_observables(b, 0, 0, 1)  # also checks the device error flag
+    finally:
+        sw.sw_batch_destroy(b)
+    lats = [sw.Lattice(int(Lr), float(br), int(sr), stream=stream.cuda_stream) for Lr, br, sr in zip(Ls, betas, seeds)]
+    try:
+        for lat in lats:
+            lat.sweep(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for lat in lats:
+            lat.sweep(n_plain)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_p = e0.elapsed_time(e1)
+        lats[0].observables(0, 1)
+    finally:
+        for lat in lats:
+            lat.close()
+    batched = sites * n_b / (ms_b / 1e3)
+    plain = sites * n_plain / (ms_p / 1e3)
+    return {"workload": "256 replicas, L_r from default_rng(4) over {64,128,256,512,1024}, "
+                        "beta_b = 0.40 + 0.08 b/63, seed 1000 + r, hot start",
+            "sites": sites, "batched_su_s": batched, "batched_sweeps": n_b,
+            "batched_ms_per_sweep": ms_b / n_b, "plain_su_s": plain, "plain_sweeps": n_plain,
+            "plain_ms_per_sweep": ms_p / n_plain, "ratio": batched / plain,
+            "how": "batched: sw_batch_sweep graph replays of 50 sweeps; plain: sw_sweep(n) on each of the 256 "
+                   "handles in turn; CUDA events on one stream; working set > L2 (batched), each plain "
+                   "replica <= 1 MiB of spins (L2-resident)"}
+
+
+def measure_serving(sw, stream, n_requests: int, capacity_su_s: float, budget_gib: int):
+    """Poisson stream of requests with the serving mix (L log-uniform in
+    [32, 4096], beta uniform in [0.30, 0.60], sweeps uniform in [100, 10000],
+    seeds from default_rng(5)) at 80% of the batched capacity; latency from
+    arrival to result on the host."""
+    from workloads import serving_requests
+    from paper_2302_14720_gb300.serving import Request, Server, latency_summary
+    mean_su = 8.73e9   # E[L^2] * E[sweeps] of the mix
+    rate = 0.8 * capacity_su_s / mean_su
+    stream_reqs = serving_requests(n=n_requests, rate_per_s=rate, seed=5)
+    reqs = [Request(i, L=q["L"], beta=q["beta"], seed=q["seed"], sweeps=q["sweeps"], arrival=q["arrival"])
+            for i, q in enumerate(stream_reqs)]
+    with Server(budget_bytes=budget_gib << 30, chunk=64, stream=stream.cuda_stream) as srv:
+        t0 = time.perf_counter()
+        res = srv.run(reqs, realtime=True)
+        wall = time.perf_counter() - t0
+        su = srv.site_updates
+        steps = srv.steps
+    for r in res:
+        if r.error is None:
+            assert (np.abs(r.E) <= 2 * reqs[r.rid].L ** 2).all()
+    summary = latency_summary(res)
+    summary.update({"requests": n_requests, "rate_per_s": rate, "budget_gib": budget_gib,
+                    "aggregate_su_s": su / wall, "site_updates": su, "wall_s": wall, "chunks": steps,
+                    "workload": "Poisson arrivals at 0.8 x batched capacity / 8.73e9 SU per request; "
+                                "L = round(exp(U[ln 32, ln 4096])), beta ~ U[0.30, 0.60], "
+                                "sweeps ~ U{100..10000}, default_rng(5)"})
+    return summary
 
 
 def sw_source_hash() -> str:
@@ -332,6 +427,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=3)
+    ap.add_argument("--batched-sweeps", type=int, default=500,
+                    help="sweeps of the 256-replica batch (0 skips the batched and serving measurements)")
+    ap.add_argument("--plain-sweeps", type=int, default=100, help="sweeps of each replica run alone")
+    ap.add_argument("--serving-requests", type=int, default=100, help="requests of the serving run (0 skips it)")
+    ap.add_argument("--serving-budget-gib", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
