@@ -3,7 +3,7 @@
 // the tiles of all active replicas; a replica's tiles find its descriptor
 // (geometry, threshold, key schedule, buffers, counter, trace row) in a
 // device table. An n-sweep sequence (3 phases + a counter advance per sweep)
-// is captured once as a CUDA graph and replayed until n, the power-of-two
+// is captured once per n as a CUDA graph and replayed until the power-of-two
 // bucket of the tile count or a table's capacity changes.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -14,6 +14,7 @@
 
 #include <cstdio>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "sw.h"
@@ -68,8 +69,9 @@ struct sw_batch {
   int grid_tiles = 0;   // launch width: ntiles rounded up to a power of two
   bool dirty = true;        // tile map and descriptors must be rebuilt
   bool descs_stale = true;  // descriptors must be uploaded
-  cudaGraphExec_t graph = nullptr;
-  int graph_n = 0;
+  // Captured n-sweep graphs, one per n in use (a server runs a few chunk
+  // lengths); all are dropped when a launch width or a table moves.
+  std::vector<std::pair<int, cudaGraphExec_t>> graphs;
 };
 
 namespace {
@@ -88,10 +90,11 @@ int cuda_bfail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_bfail(e_, what); \
   } while (0)
 
+constexpr size_t kMaxGraphs = 16;
+
 void drop_graph(sw_batch* b) {
-  if (b->graph) cudaGraphExecDestroy(b->graph);
-  b->graph = nullptr;
-  b->graph_n = 0;
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
+  b->graphs.clear();
 }
 
 sw::ReplicaDesc desc_of(const sw_batch* b, const Replica& r) {
@@ -345,8 +348,14 @@ int sw_batch_sweep(sw_batch* b, int32_t n) {
   if (rc != SW_OK) return rc;
   if (b->ntiles == 0) return SW_OK;
   sw::BatchArgs ba{b->d_descs, b->d_tile_rep, b->desc_cap};
-  if (!b->graph || b->graph_n != n) {
-    drop_graph(b);
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : b->graphs)
+    if (g.first == n) exec = g.second;
+  if (!exec) {
+    if (b->graphs.size() >= kMaxGraphs) {
+      cudaGraphExecDestroy(b->graphs.front().second);
+      b->graphs.erase(b->graphs.begin());
+    }
     cudaGraph_t g = nullptr;
     B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
     cudaError_t e = cudaSuccess;
@@ -358,15 +367,12 @@ int sw_batch_sweep(sw_batch* b, int32_t n) {
     }
     const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
     if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      b->graph = nullptr;
-      return cuda_bfail(e, "graph capture of the batch sweep");
-    }
-    b->graph_n = n;
+    if (e != cudaSuccess) return cuda_bfail(e, "graph capture of the batch sweep");
+    b->graphs.emplace_back(n, exec);
   }
-  B_CUDA(cudaGraphLaunch(b->graph, b->stream), "graph launch");
+  B_CUDA(cudaGraphLaunch(exec, b->stream), "graph launch");
   for (Replica& r : b->reps)
     if (r.active) r.t += (r.t_end - r.t < n ? r.t_end - r.t : n);
   return SW_OK;
