@@ -708,6 +708,41 @@ __global__ void phase2_kernel(const SweepArgs a0, const BatchArgs bat) {
   }
 }
 
+// ------------------------------------------------------------- resolve
+
+// Runs after every union of the sweep is done. Each slot node of the tile
+// is rewritten to name its component's root directly, together with the
+// root's key (the component's minimum site, C9) and the flip decision drawn
+// for it (C6): bits 0-31 root node, 32-62 root key, 63 flip. Keys are site
+// indices below 2^31, so bit 63 is free. Walks only read; a thread writes
+// only its own node, and the parent field it leaves (the root) is an
+// ancestor, so walks of other threads that meet a rewritten node still end
+// at the same root. Phase 3 then reads a slot's decision in one load.
+template <int WPR, int TH, int H, bool BATCH>
+__global__ void resolve_kernel(const SweepArgs a0, const BatchArgs bat) {
+  constexpr int MS = Tile<WPR, TH, H>::MS;
+  SweepArgs a;
+  int tile;
+  if (!cta_args<BATCH>(a0, bat, a, tile)) return;
+  const int nsl = min(a.tb.nslots[tile], MS);
+  for (int j = threadIdx.x; j < nsl; j += blockDim.x) {
+    const uint32_t x = (uint32_t)tile * MS + j;
+    uint32_t cur = x;
+    uint64_t v = ld_node(a.tb.nodes + cur);
+    for (int it = 0; (uint32_t)v != cur; ++it) {
+      if (it >= kGlobalFindCap) {
+        atomicCAS(a.tb.err, 0, kErrUnionCap);
+        break;
+      }
+      cur = (uint32_t)v;
+      v = ld_node(a.tb.nodes + cur);
+    }
+    const uint32_t key = (uint32_t)(v >> 32) & 0x7fffffffu;
+    const uint32_t f = flip_bit(key, a.t, a.ks);
+    a.tb.nodes[x] = ((uint64_t)(key | (f << 31)) << 32) | cur;
+  }
+}
+
 // ================================================================ phase 3
 
 // MODE 0: flips + E/M; 1: flips + E/M + cluster sizes; 2: canonical labels.
@@ -769,11 +804,10 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
   const int nsl = a.tb.nslots[P.tile];
   if (block_popc_prefix<RW, NT>(s_bmask, s_pre, s_wsum) != nsl && tid == 0) atomicCAS(a.tb.err, 0, kErrSlotOverflow);
 
-  // ---- global roots of this tile's slots
+  // ---- this tile's slots: root key and flip, as the resolve pass left them
   for (int j = tid; j < nsl; j += NT) {
-    const uint64_t v = find_global(a.tb.nodes, (uint32_t)P.tile * MS + j, a.tb.err);
-    const uint32_t key = (uint32_t)(v >> 32);
-    s_slotval[j] = LABELS ? (int)key : (int)flip_bit(key, a.t, a.ks);
+    const uint64_t v = ld_node(a.tb.nodes + (uint32_t)P.tile * MS + j);
+    s_slotval[j] = LABELS ? (int)((uint32_t)(v >> 32) & 0x7fffffffu) : (int)(v >> 63);
     if (HIST) s_slotroot[j] = (uint32_t)v;
   }
   __syncthreads();
@@ -868,9 +902,9 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
         atomicCAS(a.tb.err, 0, kErrSlotOverflow);
         slot = 0;
       }
-      const uint64_t v = find_global(a.tb.nodes, (uint32_t)tileE * MS + slot, a.tb.err);
+      const uint64_t v = ld_node(a.tb.nodes + (uint32_t)tileE * MS + slot);
       const uint32_t old = (bbits[T::OFF_HE + (y >> 5)] >> (y & 31)) & 1u;
-      bit = (old ^ flip_bit((uint32_t)(v >> 32), a.t, a.ks)) != 0u;
+      bit = (old ^ (uint32_t)(v >> 63)) != 0u;
     }
     const uint32_t m = __ballot_sync(0xffffffffu, bit);
     if (lane == 0) s_hEnew[b0 >> 5] = m;
@@ -885,9 +919,9 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
         atomicCAS(a.tb.err, 0, kErrSlotOverflow);
         slot = 0;
       }
-      const uint64_t v = find_global(a.tb.nodes, (uint32_t)tileS * MS + slot, a.tb.err);
+      const uint64_t v = ld_node(a.tb.nodes + (uint32_t)tileS * MS + slot);
       const uint32_t old = (bbits[T::OFF_HS + (x >> 5)] >> (x & 31)) & 1u;
-      bit = (old ^ flip_bit((uint32_t)(v >> 32), a.t, a.ks)) != 0u;
+      bit = (old ^ (uint32_t)(v >> 63)) != 0u;
     }
     const uint32_t m = __ballot_sync(0xffffffffu, bit);
     if (lane == 0) s_hSnew[b0 >> 5] = m;
@@ -1053,6 +1087,7 @@ cudaError_t launch_all(int which, const SweepArgs& a, int mode, uint8_t* out, cu
       break;
     case 2:
       phase2_kernel<WPR, TH, H, false><<<ntiles, TH + T::TW, 0, st>>>(a, BatchArgs{});
+      resolve_kernel<WPR, TH, H, false><<<ntiles, 128, 0, st>>>(a, BatchArgs{});
       break;
     case 3:
       if (mode == 0) {
@@ -1076,6 +1111,7 @@ cudaError_t launch_all(int which, const SweepArgs& a, int mode, uint8_t* out, cu
       break;
     case 12:
       phase2_kernel<WPR, TH, H, true><<<ntiles, TH + T::TW, 0, st>>>(a, *batch);
+      resolve_kernel<WPR, TH, H, true><<<ntiles, 128, 0, st>>>(a, *batch);
       break;
     case 13:
       phase3_kernel<WPR, TH, H, 0, true><<<ntiles, T::NT, 0, st>>>(a, *batch);
