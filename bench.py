@@ -158,14 +158,25 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(rank: int) -> int:
+    """Rank 0 runs the configured chain; the others independent replicas."""
+    return SEED + rank
+
+
+def whole_job_rate(units_per_rank: int, local_ms: float, world: int, device: str = "cuda") -> tuple[float, float]:
+    """Units all ranks processed / the slowest rank's time: (rate, max ms)."""
+    max_ms = max_over_ranks(local_ms, world, device)
+    return world * units_per_rank / (max_ms / 1e3), max_ms
 
 
 # -------------------------------------------------------------- reference
@@ -218,7 +229,7 @@ def run_ours(args):
     # the timing events, so the events bracket exactly the sweep's kernels.
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    seed = SEED + rank  # rank 0 runs the configured chain; other ranks are independent replicas
+    seed = replica_seed(rank)
     lat = sw.Lattice(L, BETA, seed, sw.SW_INIT_HOT, stream=stream.cuda_stream)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -249,8 +260,7 @@ def run_ours(args):
     total_ms = sum(step_ms)
     E, M = lat.observables(t_first, args.steps)
     assert (np.abs(E) <= 2 * N_SITES).all() and (np.abs(M) <= N_SITES).all()
-    max_ms = max_over_ranks(total_ms, world)
-    value = world * N_SITES * args.steps / (max_ms / 1e3)
+    value, max_ms = whole_job_rate(N_SITES * args.steps, total_ms, world)
 
     # ---- roofline of the dominant kernel (largest summed device time)
     ntiles = (L // TW) * (L // TH)
@@ -294,6 +304,10 @@ def run_ours(args):
 
     if rank != 0:
         return 0
+    others = None
+    if not args.no_configs:
+        others = measure_other_configs(sw, torch, stream, flush)
+        log("configs:", json.dumps(others))
     batched = serving = None
     if args.batched_sweeps > 0:
         batched = measure_batched(sw, torch, stream, args.batched_sweeps, args.plain_sweeps)
@@ -323,11 +337,71 @@ def run_ours(args):
         # phase 2 is two launches (the merge and the resolve pass)
         "gpu_launches": int(phase_n[0] + 2 * phase_n[1] + phase_n[2]),
         "clocks": clock_info,
+        "other_configs": others,
         "batched_vs_plain": batched,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def timed_sweeps(torch, stream, fn, n: int) -> float:
+    """Device milliseconds of fn() (which issues n sweeps) on `stream`."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_other_configs(sw, torch, stream, flush):
+    """The smaller configurations and the second temperature of the headline
+    lattice: per-sweep latency at L=64, the L2-resident rate with per-sweep
+    cluster histograms at L=1024, and L=8192 at beta=0.50."""
+    out = {}
+    # L=64, beta_c, hot start seed 1: 1000 sweeps, plain launches and as a
+    # one-replica batch (one CUDA graph of 100 sweeps per call)
+    with sw.Lattice(64, BETA, 1, stream=stream.cuda_stream) as lat:
+        lat.sweep(10)
+        ms = timed_sweeps(torch, stream, lambda: lat.sweep(1000), 1000)
+        lat.observables(0, 1)
+    b = sw.sw_batch_create([64], [BETA], [1], stream=stream.cuda_stream)
+    try:
+        sw.sw_batch_sweep(b, 100)
+        ms_g = timed_sweeps(torch, stream, lambda: [sw.sw_batch_sweep(b, 100) for _ in range(10)], 1000)
+        sw.sw_batch_observables(b, 0, 0, 1)
+    finally:
+        sw.sw_batch_destroy(b)
+    out["L64_betac"] = {"us_per_sweep": 1e3 * ms / 1000, "us_per_sweep_graph": 1e3 * ms_g / 1000,
+                        "su_s": 64 * 64 * 1000 / (ms / 1e3), "sweeps": 1000,
+                        "how": "sw_sweep(1000) launches; and a one-replica batch replaying a 100-sweep graph"}
+    # L=1024, beta_c, cold start seed 2, histogram every sweep (L2-resident)
+    with sw.Lattice(1024, BETA, 2, sw.SW_INIT_COLD, stream=stream.cuda_stream) as lat:
+        lat.histogram(True)
+        lat.sweep(20)
+        n = 1000
+        ms = timed_sweeps(torch, stream, lambda: lat.sweep(n), n)
+        h = lat.histograms(20, n)
+        assert (h[:, 1] > 0).all()
+        lat.histogram(False)
+        ms_nh = timed_sweeps(torch, stream, lambda: lat.sweep(n), n)
+    out["L1024_betac_cold_hist"] = {"su_s": 1024 * 1024 * n / (ms / 1e3), "us_per_sweep": 1e3 * ms / n,
+                                    "su_s_without_hist": 1024 * 1024 * n / (ms_nh / 1e3), "sweeps": n,
+                                    "l2": "state L2-resident (1 MiB spins), no flush"}
+    # L=8192, beta=0.50, hot start seed 3, L2 flushed between sweeps
+    with sw.Lattice(L, 0.50, SEED, stream=stream.cuda_stream) as lat:
+        for k in range(3):
+            flush.fill_(k)
+            lat.sweep(1)
+        tot = 0.0
+        for k in range(10):
+            flush.fill_(k + 3)
+            tot += timed_sweeps(torch, stream, lambda: lat.sweep(1), 1)
+        lat.observables(3, 10)
+    out["L8192_beta0.50"] = {"su_s": N_SITES * 10 / (tot / 1e3), "ms_per_sweep": tot / 10, "sweeps": 10}
+    return out
 
 
 def measure_batched(sw, torch, stream, n_batched: int, n_plain: int):
@@ -428,6 +502,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=3)
+    ap.add_argument("--no-configs", action="store_true", help="skip the L=64, L=1024 and beta=0.50 lines")
     ap.add_argument("--batched-sweeps", type=int, default=500,
                     help="sweeps of the 256-replica batch (0 skips the batched and serving measurements)")
     ap.add_argument("--plain-sweeps", type=int, default=100, help="sweeps of each replica run alone")

@@ -39,6 +39,9 @@
  *      x0 >> 31 == 1; then every site of it takes s <- -s. (The paper's
  *      §2.4 assigns each cluster a fresh random spin; with monochrome
  *      clusters both rules give the same distribution.)
+ *  C6b Assignment rule (optional, sw_set_rule / sw_batch_set_rule, §2.4 as
+ *      printed): counter (root, t, 3, 0), word x0; every site of the
+ *      cluster takes s = (x0>>31) ? -1 : +1, whatever its old spin.
  *  C7  Hot start: counter (site, 0, 2, 0), word x0; s = (x0>>31) ? -1 : +1.
  *      Cold start: every spin +1.
  *  C8  Sweep counter t starts at 0 at creation and grows by one per sweep,
@@ -87,6 +90,9 @@ extern "C" {
 #define SW_INIT_HOT  0
 #define SW_INIT_COLD 1
 
+#define SW_RULE_FLIP   0  /* C6: each cluster flips with probability 1/2 (default) */
+#define SW_RULE_ASSIGN 1  /* C6b: each cluster gets a fresh spin (§2.4 as printed) */
+
 /* int64 words per sweep written by sw_histograms: n_clusters, sum |C|^2, 32 bins (C11). */
 #define SW_HIST_WORDS 34
 
@@ -122,7 +128,10 @@ int sw_destroy(sw_lattice* h);
  * sweep E and M (C10), and the C11 statistics if enabled, are appended to
  * the device-side trace. Errors: SW_EINVAL (n < 0), SW_ENOMEM (trace
  * growth), SW_ECUDA. Device-side failures are reported by the next call that
- * synchronises. */
+ * synchronises. A lattice with L <= 181 and statistics off runs all n
+ * sweeps in one CTA-sized launch (the whole lattice in shared memory)
+ * unless the environment variable SW_TILE_SHAPE was set at sw_create, which
+ * keeps it on the tiled path; the results are the same. */
 int sw_sweep(sw_lattice* h, int32_t n);
 
 /* Current sweep counter t (the counter the next sweep will use). */
@@ -139,6 +148,10 @@ int sw_observables(sw_lattice* h, int64_t first, int64_t count,
 /* Enable (1) or disable (0) the per-sweep C11 cluster statistics for the
  * sweeps that follow. Sweeps run while disabled read back as zeros. */
 int sw_histogram(sw_lattice* h, int32_t enable);
+
+/* New-spin rule of the sweeps that follow: SW_RULE_FLIP (C6, the default)
+ * or SW_RULE_ASSIGN (C6b, §2.4). Any other value: SW_EINVAL. */
+int sw_set_rule(sw_lattice* h, int32_t rule);
 
 /* Copy the C11 statistics of sweeps [first, first+count) to
  * out_host[count][SW_HIST_WORDS] (int64, row per sweep). Same range rules
@@ -220,6 +233,10 @@ int sw_batch_sweep(sw_batch* b, int32_t n);
  * negative value removes the limit. */
 int sw_batch_set_limit(sw_batch* b, int32_t slot, int64_t sweeps_left);
 
+/* New-spin rule (SW_RULE_FLIP or SW_RULE_ASSIGN) of the replica in `slot`
+ * for the sweeps that follow. */
+int sw_batch_set_rule(sw_batch* b, int32_t slot, int32_t rule);
+
 /* Sweep counter of the replica in `slot`. */
 int sw_batch_get_sweep(sw_batch* b, int32_t slot, uint32_t* t_out);
 
@@ -264,7 +281,9 @@ int sw_batch_destroy(sw_batch* b);
  *  err    : device int32 [1], output: set to 0 by the call, then to a
  *           nonzero code if a capped device retry loop gave up.
  *  stream : cudaStream_t for all work (NULL = the legacy default stream).
- * The kernels' working buffers live in one file-scope __device__ array of
+ * For L <= 181 the whole lattice is swept inside one CTA's shared memory
+ * and nothing else is used. For larger L the kernels' working buffers live
+ * in one file-scope __device__ array of
  * under 4 MiB that every GPU loading the library holds until exit. The first
  * call on a device looks up that array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.

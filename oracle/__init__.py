@@ -16,6 +16,9 @@ each function (what pins it, in tests/test_oracle_*.py):
   labels      -- scipy.sparse.csgraph.connected_components and a union-find
                  written differently in the test; canonical-min invariants
   flip        -- clusters stay monochrome; spin-reversal symmetry
+  assign      -- clusters end monochrome; the result ignores the old spins;
+                 equals a flip by the old-vs-new difference; exact 2x2
+                 transition matrix and 4x4 moments of the assign chain
   observe     -- closed forms of ordered, checkerboard and striped states
   histogram   -- against cluster sizes from scipy's labelling
   run         -- exact 2x2 transition matrix (detailed balance), 3x3 state
@@ -74,12 +77,16 @@ def _load():
         lib.oracle_flip.restype = None
         lib.oracle_apply_flips.argtypes = [ctypes.c_int, P, P, P]
         lib.oracle_apply_flips.restype = None
+        lib.oracle_assign.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, P, P]
+        lib.oracle_assign.restype = None
+        lib.oracle_apply_assign.argtypes = [ctypes.c_int, P, P, P]
+        lib.oracle_apply_assign.restype = None
         lib.oracle_observe.argtypes = [ctypes.c_int, P, P, P]
         lib.oracle_observe.restype = None
         lib.oracle_histogram.argtypes = [ctypes.c_int, P, P, P]
         lib.oracle_histogram.restype = None
         lib.oracle_run.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
-                                   ctypes.c_int, P, P, P, P]
+                                   ctypes.c_int, P, P, P, P, ctypes.c_int]
         lib.oracle_run.restype = ctypes.c_int
         _lib = lib
         return lib
@@ -156,6 +163,25 @@ def apply_flips(spins: np.ndarray, lab: np.ndarray, flip_of_root: np.ndarray) ->
     return s
 
 
+def assign(spins_shape_L: int, lab: np.ndarray, seed: int, t: int) -> np.ndarray:
+    """New spins by §2.4's assignment: cluster rooted at r gets -1 iff
+    Philox (r,t,3,0).x0 >> 31, whatever its old spin."""
+    L = int(spins_shape_L)
+    s = np.zeros((L, L), dtype=np.int8)
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    _load().oracle_assign(L, seed, t & 0xffffffff, _ptr(lab), _ptr(s))
+    return s
+
+
+def apply_assign(L: int, lab: np.ndarray, minus_of_root: np.ndarray) -> np.ndarray:
+    """New spins with an explicit 0/1 (1 = -1) value stored at each root."""
+    s = np.zeros((L, L), dtype=np.int8)
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    m = np.ascontiguousarray(minus_of_root, dtype=np.uint8).reshape(-1)
+    _load().oracle_apply_assign(L, _ptr(lab), _ptr(m), _ptr(s))
+    return s
+
+
 def observe(spins: np.ndarray):
     """(E, M) of a state: E over the 2N edges, M = sum of spins (end of §2)."""
     s = np.ascontiguousarray(spins, dtype=np.int8)
@@ -175,9 +201,13 @@ def histogram(lab: np.ndarray) -> np.ndarray:
     return hist
 
 
+RULES = {"flip": 0, "assign": 1}
+
+
 def run(L: int, beta: float, seed: int, n: int, *, spins: np.ndarray | None = None,
-        cold: bool = False, t0: int = 0, hist: bool = False):
-    """Run n sweeps (counters t0..t0+n-1) from spins (or the C7 start).
+        cold: bool = False, t0: int = 0, hist: bool = False, rule: str = "flip"):
+    """Run n sweeps (counters t0..t0+n-1) from spins (or the C7 start);
+    rule "flip" (C6) or "assign" (§2.4 as printed).
 
     Returns (final spins int8 [L, L], E int64 [n], M int64 [n], hist int64
     [n, 34] or None).
@@ -192,7 +222,7 @@ def run(L: int, beta: float, seed: int, n: int, *, spins: np.ndarray | None = No
     M = np.zeros(max(n, 1), dtype=np.int64)
     H = np.zeros((max(n, 1), HIST_WORDS), dtype=np.int64) if hist else None
     rc = _load().oracle_run(L, float(beta), seed, t0 & 0xffffffff, n, _ptr(s), _ptr(E), _ptr(M),
-                            _ptr(H) if hist else None)
+                            _ptr(H) if hist else None, RULES[rule])
     if rc != 0:
         raise MemoryError("oracle_run: allocation failed")
     return s, E[:n], M[:n], (H[:n] if hist else None)

@@ -181,6 +181,25 @@ void oracle_apply_flips(int L, const int32_t* label, const uint8_t* flip_of_root
         if (flip_of_root[label[i]]) s[i] = (int8_t)(-s[i]);
 }
 
+/* §2.4 as the paper prints it (the assignment reading): every cluster gets
+ * a fresh spin, -1 iff the top bit of word x0 of Philox block (r, t, 3, 0)
+ * is set, r = the cluster's root; the old spins are not read. */
+void oracle_assign(int L, uint64_t seed, uint32_t t, const int32_t* label, int8_t* s) {
+    int64_t N = (int64_t)L * L;
+    for (int64_t i = 0; i < N; ++i) {
+        uint32_t w[4];
+        philox_seeded(seed, (uint32_t)label[i], t, 3u, 0u, w);
+        s[i] = (w[0] >> 31) ? (int8_t)-1 : (int8_t)1;
+    }
+}
+
+/* Apply an explicit new spin per cluster: minus_of_root[r] (0/1, 1 = -1) is
+ * read at the root r = label[i]. Used by exact transition-matrix tests. */
+void oracle_apply_assign(int L, const int32_t* label, const uint8_t* minus_of_root, int8_t* s) {
+    int64_t N = (int64_t)L * L;
+    for (int64_t i = 0; i < N; ++i) s[i] = minus_of_root[label[i]] ? (int8_t)-1 : (int8_t)1;
+}
+
 /* ------------------------------------------------------------ observables */
 
 /* End of §2: H = -sum over nearest-neighbour pairs of s_i s_j (each of the
@@ -224,10 +243,11 @@ void oracle_histogram(int L, const int32_t* label, int64_t* hist, int64_t* count
 
 /* Run n sweeps with counters t0 .. t0+n-1 from the state s (updated in
  * place). E_out/M_out[n] receive the observables after each sweep;
- * hist_out (nullable) receives 34 words per sweep. Returns 0, or -1 on
- * allocation failure. */
+ * hist_out (nullable) receives 34 words per sweep. rule 0 flips clusters
+ * (oracle_flip), rule 1 assigns them fresh spins (oracle_assign). Returns
+ * 0, or -1 on allocation failure. */
 int oracle_run(int L, double beta, uint64_t seed, uint32_t t0, int n, int8_t* s,
-               int64_t* E_out, int64_t* M_out, int64_t* hist_out) {
+               int64_t* E_out, int64_t* M_out, int64_t* hist_out, int rule) {
     int64_t N = (int64_t)L * L;
     uint32_t thr = oracle_threshold(beta);
     uint8_t* bonds = (uint8_t*)malloc((size_t)N);
@@ -242,7 +262,8 @@ int oracle_run(int L, double beta, uint64_t seed, uint32_t t0, int n, int8_t* s,
         uint32_t t = t0 + (uint32_t)k;
         oracle_bonds(L, seed, t, thr, s, bonds);
         oracle_labels(L, bonds, label, queue);
-        oracle_flip(L, seed, t, label, s);
+        if (rule == 1) oracle_assign(L, seed, t, label, s);
+        else oracle_flip(L, seed, t, label, s);
         oracle_observe(L, s, &E_out[k], &M_out[k]);
         if (hist_out) oracle_histogram(L, label, hist_out + 34 * (int64_t)k, count);
     }

@@ -28,6 +28,8 @@ SW_EDEVICE = -4
 SW_ETIMEOUT = -5
 SW_INIT_HOT = 0
 SW_INIT_COLD = 1
+SW_RULE_FLIP = 0
+SW_RULE_ASSIGN = 1
 SW_HIST_WORDS = 34
 
 _STATUS_NAMES = {SW_EINVAL: "SW_EINVAL", SW_ENOMEM: "SW_ENOMEM", SW_ECUDA: "SW_ECUDA",
@@ -44,6 +46,7 @@ SIGNATURES = {
     "sw_get_sweep": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32)]),
     "sw_observables": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
     "sw_histogram": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sw_set_rule": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sw_histograms": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P]),
     "sw_labels": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "sw_spins": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
@@ -57,6 +60,7 @@ SIGNATURES = {
     "sw_batch_remove": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sw_batch_sweep": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sw_batch_footprint": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "sw_batch_set_rule": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sw_batch_set_limit": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
     "sw_batch_get_sweep": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32)]),
     "sw_batch_observables": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _P]),
@@ -142,6 +146,10 @@ def sw_observables(h: int, first: int, count: int):
 
 def sw_histogram(h: int, enable: bool) -> None:
     _check(_lib.sw_histogram(h, 1 if enable else 0), "sw_histogram")
+
+
+def sw_set_rule(h: int, rule: int) -> None:
+    _check(_lib.sw_set_rule(h, int(rule)), "sw_set_rule")
 
 
 def sw_histograms(h: int, first: int, count: int) -> np.ndarray:
@@ -256,6 +264,10 @@ def sw_batch_sweep(b: int, n: int) -> None:
     _check(_lib.sw_batch_sweep(b, int(n)), "sw_batch_sweep")
 
 
+def sw_batch_set_rule(b: int, slot: int, rule: int) -> None:
+    _check(_lib.sw_batch_set_rule(b, int(slot), int(rule)), "sw_batch_set_rule")
+
+
 def sw_batch_set_limit(b: int, slot: int, sweeps_left: int) -> None:
     _check(_lib.sw_batch_set_limit(b, int(slot), int(sweeps_left)), "sw_batch_set_limit")
 
@@ -324,6 +336,9 @@ class Lattice:
 
     def histogram(self, enable: bool) -> None:
         sw_histogram(self.h, enable)
+
+    def set_rule(self, rule: int) -> None:
+        sw_set_rule(self.h, rule)
 
     def spins(self) -> np.ndarray:
         return sw_spins(self.h, self.L)

@@ -97,6 +97,8 @@ struct sw_lattice {
   int shape = 0;
   int device = 0;
   bool hist_on = false;
+  bool tiles_only = false;  // SW_TILE_SHAPE was set: always the tiled path
+  int rule = SW_RULE_FLIP;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   sw::Geometry g{};
@@ -180,6 +182,7 @@ sw::SweepArgs args_of(const sw_lattice* h) {
   a.g = h->g;
   a.thr = h->thr;
   a.t = (uint32_t)h->t;
+  a.rule = (uint32_t)h->rule;
   a.ks = h->ks;
   a.tb = h->tb;
   a.spins_in = h->spins;
@@ -278,6 +281,7 @@ int sw_create(int32_t L, double beta, uint64_t seed, int32_t init, void* stream,
   h->seed = seed;
   h->thr = threshold_of(beta);
   h->shape = shape_for(L);
+  h->tiles_only = getenv("SW_TILE_SHAPE") != nullptr;
   h->ks = sw::make_key_schedule(seed);
   cudaGetDevice(&h->device);
   const sw::TileShape ts = sw::shape_of(h->shape);
@@ -338,6 +342,22 @@ int sw_sweep(sw_lattice* h, int32_t n) {
   if (rc != SW_OK) return rc;
   const sw::TileShape ts = sw::shape_of(h->shape);
   (void)ts;
+  if (h->L <= sw::kSmallMaxL && !h->hist_on && !h->tiles_only) {
+    // the whole lattice fits one CTA: all n sweeps in one launch
+    sw::SmallArgs s{};
+    s.L = h->L;
+    s.thr = h->thr;
+    s.rule = (uint32_t)h->rule;
+    s.t0 = (uint32_t)h->t;
+    s.n = n;
+    s.ks = h->ks;
+    s.spins = h->spins;
+    s.em = h->em + 2 * (h->t - h->t_base);
+    s.err = h->tb.err;
+    SW_CUDA(timed_phase(h, 0, [&] { return sw::launch_small(s, h->stream); }), "small-lattice sweep launch");
+    h->t += n;
+    return SW_OK;
+  }
   for (int32_t k = 0; k < n; ++k) {
     sw::SweepArgs a = args_of(h);
     const int64_t row = h->t - h->t_base;
@@ -381,6 +401,13 @@ int sw_observables(sw_lattice* h, int64_t first, int64_t count, int64_t* E_host,
     if (M_host) M_host[k] = tmp[2 * k + 1];
   }
   free(tmp);
+  return SW_OK;
+}
+
+int sw_set_rule(sw_lattice* h, int32_t rule) {
+  if (!h) return fail(SW_EINVAL, "handle is NULL");
+  if (rule != SW_RULE_FLIP && rule != SW_RULE_ASSIGN) return fail(SW_EINVAL, "rule must be SW_RULE_FLIP or SW_RULE_ASSIGN");
+  h->rule = rule;
   return SW_OK;
 }
 

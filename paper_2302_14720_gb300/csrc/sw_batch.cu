@@ -28,6 +28,7 @@ struct Replica {
   double beta = 0.0;
   uint64_t seed = 0;
   uint32_t thr = 0;
+  int rule = SW_RULE_FLIP;
   int64_t t = 0;       // counter of the next sweep (host mirror of the device value)
   int64_t t_end = INT64_MAX;  // the replica stops before this counter
   int64_t t_base = 0;  // first sweep in the trace
@@ -106,6 +107,7 @@ sw::ReplicaDesc desc_of(const sw_batch* b, const Replica& r) {
   d.a.g.tiles_y = (r.L + ts.th - 1) / ts.th;
   d.a.g.aligned16 = (r.L % 16) == 0;
   d.a.thr = r.thr;
+  d.a.rule = (uint32_t)r.rule;
   d.a.ks = sw::make_key_schedule(r.seed);
   d.a.tb = r.tb;
   d.a.spins_in = r.spins;
@@ -383,6 +385,15 @@ int sw_batch_set_limit(sw_batch* b, int32_t slot, int64_t sweeps_left) {
   if (rc != SW_OK) return rc;
   Replica& r = b->reps[slot];
   r.t_end = sweeps_left < 0 ? INT64_MAX : r.t + sweeps_left;
+  b->descs_stale = true;
+  return SW_OK;
+}
+
+int sw_batch_set_rule(sw_batch* b, int32_t slot, int32_t rule) {
+  int rc = check_slot(b, slot);
+  if (rc != SW_OK) return rc;
+  if (rule != SW_RULE_FLIP && rule != SW_RULE_ASSIGN) return bfail(SW_EINVAL, "rule must be SW_RULE_FLIP or SW_RULE_ASSIGN");
+  b->reps[slot].rule = rule;
   b->descs_stale = true;
   return SW_OK;
 }

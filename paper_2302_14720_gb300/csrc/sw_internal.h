@@ -71,6 +71,7 @@ struct SweepArgs {
   Geometry g;
   uint32_t thr;        // bond threshold (C3)
   uint32_t t;          // sweep counter (C5, C6)
+  uint32_t rule;       // new spins: 0 flip each cluster with probability 1/2 (C6), 1 assign a fresh spin (§2.4)
   KeySchedule ks;      // Philox key schedule of the seed (C4)
   TileBuffers tb;
   const int8_t* spins_in;
@@ -125,6 +126,22 @@ cudaError_t launch_phase4(int shape, const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_batch_phase(int shape, int which, const BatchArgs& b, int ntiles, cudaStream_t st);
 // Batch: advance every active replica's sweep counter and trace row by one.
 cudaError_t launch_batch_advance(const BatchArgs& b, cudaStream_t st);
+
+// Whole sweeps of one small lattice in one CTA (sw_small.cu). 181^2 < 2^15,
+// so 16-bit parents index every site.
+constexpr int kSmallMaxL = 181;
+struct SmallArgs {
+  int L;
+  uint32_t thr;    // C3
+  uint32_t rule;   // 0 flip (C6), 1 assign (C6b)
+  uint32_t t0;     // counter of the first sweep
+  int n;           // sweeps to run
+  KeySchedule ks;  // C4
+  int8_t* spins;   // int8 [L][L], read at the start and written at the end
+  int64_t* em;     // [n][2] E, M after each sweep
+  int* err;        // device error flag
+};
+cudaError_t launch_small(const SmallArgs& a, cudaStream_t st);
 // Debug: expand the stored bond bits into uint8 [L][L] (bit0 east, bit1 south).
 cudaError_t launch_export_bonds(int shape, const SweepArgs& a, uint8_t* out, cudaStream_t st);
 

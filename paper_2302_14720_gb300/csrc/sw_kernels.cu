@@ -712,8 +712,9 @@ __global__ void phase2_kernel(const SweepArgs a0, const BatchArgs bat) {
 
 // Runs after every union of the sweep is done. Each slot node of the tile
 // is rewritten to name its component's root directly, together with the
-// root's key (the component's minimum site, C9) and the flip decision drawn
-// for it (C6): bits 0-31 root node, 32-62 root key, 63 flip. Keys are site
+// root's key (the component's minimum site, C9) and the decision drawn
+// for it (C6, or §2.4's assignment): bits 0-31 root node, 32-62 root key,
+// 63 decision. Keys are site
 // indices below 2^31, so bit 63 is free. Walks only read; a thread writes
 // only its own node, and the parent field it leaves (the root) is an
 // ancestor, so walks of other threads that meet a rewritten node still end
@@ -738,7 +739,7 @@ __global__ void resolve_kernel(const SweepArgs a0, const BatchArgs bat) {
       v = ld_node(a.tb.nodes + cur);
     }
     const uint32_t key = (uint32_t)(v >> 32) & 0x7fffffffu;
-    const uint32_t f = flip_bit(key, a.t, a.ks);
+    const uint32_t f = decision_bit(key, a.t, a.ks, a.rule);
     a.tb.nodes[x] = ((uint64_t)(key | (f << 31)) << 32) | cur;
   }
 }
@@ -755,7 +756,7 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
   __shared__ uint32_t s_bmask[RW];                 // border roots
   __shared__ uint32_t s_pre[RW];
   __shared__ uint32_t s_wsum[33];
-  __shared__ uint32_t s_flip[RW];                  // flip bit of every root
+  __shared__ uint32_t s_flip[RW];                  // decision bit of every root (flip, or new sign)
   __shared__ uint32_t s_snew[TH][WPR];
   __shared__ int s_slotval[MS];                    // flip bit (flip modes) or canonical label (labels mode)
   __shared__ uint32_t s_slotroot[HIST ? MS : 1];
@@ -812,8 +813,8 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
   }
   __syncthreads();
 
-  // ---- flip bit of every root of my strip: border roots from their slot,
-  // inner roots from one Philox block each (C6)
+  // ---- decision bit of every root of my strip: border roots from their slot,
+  // inner roots from one Philox block each (C6, or the assignment rule)
   if (!LABELS) {
 #pragma unroll
     for (int r = 0; r < H; ++r) {
@@ -831,7 +832,8 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
             const int sl = slot_of(s_bmask, s_pre, base + b);
             f = sl < nsl ? (uint32_t)s_slotval[sl] : 0u;
           } else {
-            f = flip_bit((uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w + b), a.t, a.ks);
+            f = decision_bit((uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w + b), a.t, a.ks,
+                             a.rule);
           }
           fl |= f << b;
         }
@@ -882,7 +884,7 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
       tmask ^= tmask << 4;
       tmask ^= tmask << 8;
       tmask ^= tmask << 16;
-      snew[r] = s[r] ^ (tmask & wmask);
+      snew[r] = (a.rule ? 0u : s[r]) ^ (tmask & wmask);
       store_spin_bits(a.spins_out + (size_t)(P.y0 + y) * L + P.x0 + 32 * w, snew[r], nb, g.aligned16);
     }
   }
@@ -904,7 +906,7 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
       }
       const uint64_t v = ld_node(a.tb.nodes + (uint32_t)tileE * MS + slot);
       const uint32_t old = (bbits[T::OFF_HE + (y >> 5)] >> (y & 31)) & 1u;
-      bit = (old ^ (uint32_t)(v >> 63)) != 0u;
+      bit = ((a.rule ? 0u : old) ^ (uint32_t)(v >> 63)) != 0u;
     }
     const uint32_t m = __ballot_sync(0xffffffffu, bit);
     if (lane == 0) s_hEnew[b0 >> 5] = m;
@@ -921,7 +923,7 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
       }
       const uint64_t v = ld_node(a.tb.nodes + (uint32_t)tileS * MS + slot);
       const uint32_t old = (bbits[T::OFF_HS + (x >> 5)] >> (x & 31)) & 1u;
-      bit = (old ^ (uint32_t)(v >> 63)) != 0u;
+      bit = ((a.rule ? 0u : old) ^ (uint32_t)(v >> 63)) != 0u;
     }
     const uint32_t m = __ballot_sync(0xffffffffu, bit);
     if (lane == 0) s_hSnew[b0 >> 5] = m;

@@ -8,7 +8,9 @@
 // synchronisation is not acceptable. For them this entry point runs the same
 // three sweep kernels as sw_sweep, on spins, an E/M output and an error word
 // that the caller owns, with the kernels' working buffers taken from one
-// file-scope device array instead of from allocations.
+// file-scope device array instead of from allocations. A lattice of side at
+// most 181 needs no buffers at all: it is swept inside one CTA's shared
+// memory (sw_small.cu).
 //
 // The array is a static __device__ object, so every GPU that loads the
 // library holds it (kNoallocScratchBytes, under 4 MiB) until the process
@@ -98,6 +100,24 @@ extern "C" int sw_sweep_noalloc(int8_t* spins, int32_t L, double beta, uint64_t 
     return sw::record_error(SW_EINVAL, "sw_sweep_noalloc: L must be in [2, SW_NOALLOC_MAX_L = 1024]");
   if (!(beta >= 0.0) || isinf(beta)) return sw::record_error(SW_EINVAL, "sw_sweep_noalloc: beta must be finite and >= 0");
   if (n < 0) return sw::record_error(SW_EINVAL, "sw_sweep_noalloc: n must be >= 0");
+  cudaStream_t st0 = (cudaStream_t)stream;
+  if (L <= sw::kSmallMaxL) {
+    // the whole lattice fits one CTA's shared memory: no scratch at all
+    sw::SmallArgs s{};
+    s.L = L;
+    s.thr = threshold_for(beta);
+    s.rule = 0;
+    s.t0 = t0;
+    s.n = n;
+    s.ks = sw::make_key_schedule(seed);
+    s.spins = spins;
+    s.em = em;
+    s.err = err;
+    cudaError_t e0 = cudaMemsetAsync(err, 0, sizeof(int32_t), st0);
+    if (e0 == cudaSuccess) e0 = sw::launch_small(s, st0);
+    if (e0 != cudaSuccess) return sw::record_error(SW_ECUDA, cudaGetErrorString(e0));
+    return SW_OK;
+  }
   unsigned char* base = nullptr;
   cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return sw::record_error(SW_ECUDA, cudaGetErrorString(e));

@@ -55,4 +55,17 @@ __device__ __forceinline__ uint32_t flip_bit(uint32_t root, uint32_t t, const Ke
   return philox4x32_10(make_uint4(root, t, 1u, 0u), ks).x >> 31;
 }
 
+// §2.4 as printed (the assignment rule): the cluster rooted at `root` gets
+// spin -1 in sweep t iff the top bit of word x0 of block (root, t, 3, 0) is set.
+__device__ __forceinline__ uint32_t assign_bit(uint32_t root, uint32_t t, const KeySchedule& ks) {
+  return philox4x32_10(make_uint4(root, t, 3u, 0u), ks).x >> 31;
+}
+
+// The per-cluster decision of a sweep: the flip bit (rule 0) or the new
+// spin's sign bit (rule 1). A site's new sign bit is decision ^ (rule 0 ?
+// its old sign bit : 0).
+__device__ __forceinline__ uint32_t decision_bit(uint32_t root, uint32_t t, const KeySchedule& ks, uint32_t rule) {
+  return rule ? assign_bit(root, t, ks) : flip_bit(root, t, ks);
+}
+
 }  // namespace sw

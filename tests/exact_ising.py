@@ -17,7 +17,6 @@ from __future__ import annotations
 import itertools
 import math
 
-import mpmath
 import numpy as np
 import scipy.special
 
@@ -69,6 +68,7 @@ def kaufman_logZ(m: int, n: int, K) -> mpmath.mpf:
     cosh g_l = cosh 2K coth 2K - cos(pi l / n) for l > 0, and
     g_0 = 2K + log tanh K (which changes sign at K_c).
     """
+    import mpmath  # only the Kaufman checks need arbitrary precision
     K = mpmath.mpf(K)
     c = mpmath.cosh(2 * K) / mpmath.tanh(2 * K)
 
@@ -91,6 +91,7 @@ def kaufman_logZ(m: int, n: int, K) -> mpmath.mpf:
 
 def kaufman_energy_per_site(L: int, beta: float) -> float:
     """<E>/N = -(1/N) d log Z / d beta on the L x L torus (exact)."""
+    import mpmath  # only the Kaufman checks need arbitrary precision
     with mpmath.workdps(40):
         d = mpmath.diff(lambda k: kaufman_logZ(L, L, k), mpmath.mpf(beta))
         return float(-d / (L * L))
@@ -117,15 +118,16 @@ def yang_magnetisation(beta: float) -> float:
 
 # --------------------------------------------- exact Swendsen-Wang kernel
 
-def sw_transition_matrix(L: int, beta: float, oracle) -> np.ndarray:
+def sw_transition_matrix(L: int, beta: float, oracle, rule: str = "flip") -> np.ndarray:
     """T[a, b] = probability that one Swendsen-Wang update takes state a to b.
 
     Every bond set B among the satisfied edges of a (each bonded with
-    probability p = 1 - exp(-2 beta), independently) and every flip pattern
-    of the clusters of B (each pattern with probability 2^-#clusters) is
-    enumerated. The clusters come from the oracle's labelling and the new
-    state from the oracle's flip step, so T is the kernel the oracle applies
-    when its random words are replaced by exact probabilities.
+    probability p = 1 - exp(-2 beta), independently) and every flip (or,
+    with rule="assign", new-spin) pattern of the clusters of B (each pattern
+    with probability 2^-#clusters) is enumerated. The clusters come from the
+    oracle's labelling and the new state from the oracle's flip (assign)
+    step, so T is the kernel the oracle applies when its random words are
+    replaced by exact probabilities.
     """
     states = all_states(L)
     nS = len(states)
@@ -153,6 +155,6 @@ def sw_transition_matrix(L: int, beta: float, oracle) -> np.ndarray:
             for flips in itertools.product((0, 1), repeat=nc):
                 f = np.zeros(N, np.uint8)
                 f[roots] = flips
-                s2 = oracle.apply_flips(s, lab, f)
+                s2 = oracle.apply_assign(L, lab, f) if rule == "assign" else oracle.apply_flips(s, lab, f)
                 T[a, code(s2)] += wB / 2**nc
     return T
