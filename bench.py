@@ -401,6 +401,26 @@ def measure_other_configs(sw, torch, stream, flush):
             tot += timed_sweeps(torch, stream, lambda: lat.sweep(1), 1)
         lat.observables(3, 10)
     out["L8192_beta0.50"] = {"su_s": N_SITES * 10 / (tot / 1e3), "ms_per_sweep": tot / 10, "sweeps": 10}
+    # the paper's label-equivalence labelling (§2.3) against the tile
+    # union-find, both from the same state (each includes drawing the bonds)
+    out["labels_union_find_vs_equivalence"] = {}
+    for Lc in (1024, 4096):
+        with sw.Lattice(Lc, BETA, 2, sw.SW_INIT_COLD, stream=stream.cuda_stream) as lat:
+            lat.sweep(30)
+            buf = torch.empty((Lc, Lc), dtype=torch.int32, device="cuda")
+            sw.sw_labels(lat.h, Lc, buf.data_ptr())
+            ms_uf = timed_sweeps(torch, stream, lambda: sw.sw_labels(lat.h, Lc, buf.data_ptr()), 1)
+            its = sw.sw_labels_equivalence(lat.h, Lc, buf.data_ptr())[1]
+            ms_le = timed_sweeps(torch, stream, lambda: sw.sw_labels_equivalence(lat.h, Lc, buf.data_ptr()), 1)
+        out["labels_union_find_vs_equivalence"][f"L{Lc}"] = {
+            "union_find_ms": ms_uf, "label_equivalence_ms": ms_le, "iterations": its, "speedup": ms_le / ms_uf}
+    # q = 3 Potts at its critical coupling ln(1 + sqrt 3)
+    with sw.Potts(1024, 3, 1.0050833, 4, stream=stream.cuda_stream) as pt:
+        pt.sweep(10)
+        n = 200
+        ms = timed_sweeps(torch, stream, lambda: pt.sweep(n), n)
+        pt.observables(10, n)
+    out["potts_q3_L1024_betac"] = {"su_s": 1024 * 1024 * n / (ms / 1e3), "us_per_sweep": 1e3 * ms / n, "sweeps": n}
     return out
 
 

@@ -165,6 +165,16 @@ int sw_histograms(sw_lattice* h, int64_t first, int64_t count, int64_t* out_host
  * on the handle's stream). */
 int sw_labels(sw_lattice* h, int32_t* out, int32_t out_is_device);
 
+/* The same labels as sw_labels, computed by the paper's label-equivalence
+ * iteration (§2.3: labels start as site indices; each site proposes the
+ * smallest bonded neighbour label as its label's reference; references are
+ * collapsed and every site relabelled; repeat until no proposal) instead of
+ * the tile union-find. A comparator for measurements, not used by the
+ * sweep. *iterations (may be NULL) receives the number of iterations run.
+ * Synchronises once per iteration. SW_ETIMEOUT if 2^20 iterations do not
+ * converge. */
+int sw_labels_equivalence(sw_lattice* h, int32_t* out, int32_t out_is_device, int32_t* iterations);
+
 /* Current spins, int8 [L][L] row-major, values +1/-1. Host or device out as
  * for sw_labels. */
 int sw_spins(sw_lattice* h, int8_t* out, int32_t out_is_device);
@@ -261,6 +271,58 @@ int sw_batch_footprint(sw_batch* b, int32_t L, int64_t sweeps, int64_t* bytes);
 
 /* Release the batch and all its replicas. NULL is a no-op. */
 int sw_batch_destroy(sw_batch* b);
+
+/* ---------------------------------------------------------------------------
+ * q-state Potts model (the paper's §6 generalisation of the sweep)
+ * ---------------------------------------------------------------------------
+ *  P1  States int8 in 0..q-1, 2 <= q <= 127; lattice and edges as C1.
+ *      H = -sum over the 2N edges of delta(s_i, s_j).
+ *  P2  Equal neighbours bond with probability p = 1 - exp(-beta); threshold
+ *      thr = (uint32) min(floor(ldexp(-expm1(-beta), 32)), 0xFFFFFFFF); the
+ *      bond draws are C5's, with "equal states" for "equal spins".
+ *  P3  Labels C9. New states: the cluster rooted at r takes
+ *      floor(x0 * q / 2^32), x0 = word 0 of Philox block (r, t, 3, 0).
+ *  P4  Hot start: floor(x0 * q / 2^32), x0 = word 0 of block (i, 0, 2, 0);
+ *      cold start: every state 0.
+ *  P5  Observables after each sweep, int64: E = -(number of edges joining
+ *      equal states), M = number of sites in state 0.
+ *  For q = 2 and beta = 2 beta_Ising this is the Ising sweep with the
+ *  assignment rule (C6b), state 1 <-> spin -1. The sweep runs site-parallel
+ *  kernels over global memory (a union-find over int32 parents). Rules of
+ *  the Ising handle (ownership, streams, statuses) apply.
+ * --------------------------------------------------------------------------- */
+typedef struct sw_potts sw_potts;
+
+/* Threshold P2 for beta; 0 for an invalid beta. */
+uint32_t sw_potts_threshold(double beta);
+
+/* New Potts lattice: SW_EINVAL for L outside [2, 46340], q outside 2..127,
+ * a bad beta or init; SW_ECUDA without a GPU. */
+int sw_potts_create(int32_t L, int32_t q, double beta, uint64_t seed, int32_t init, void* stream,
+                    sw_potts** out);
+
+/* n >= 0 sweeps with counters t .. t+n-1 (C8); E and M (P5) appended to the trace. */
+int sw_potts_sweep(sw_potts* h, int32_t n);
+
+/* E and M of sweeps [first, first+count) (absolute counters, as sw_observables). */
+int sw_potts_observables(sw_potts* h, int64_t first, int64_t count, int64_t* E_host, int64_t* M_host);
+
+/* Current states, int8 [L][L], host (synchronises) or device. */
+int sw_potts_states(sw_potts* h, int8_t* out, int32_t out_is_device);
+
+/* Replace the states (host or device int8 [L][L]) and set the counter to t;
+ * the trace restarts at t. A state outside 0..q-1: SW_EINVAL, state kept. */
+int sw_potts_set_state(sw_potts* h, const int8_t* states, uint32_t t, int32_t in_is_device);
+
+/* Canonical labels (C9) of the bonds the next sweep draws; the states and
+ * the counter are not changed. */
+int sw_potts_labels(sw_potts* h, int32_t* out, int32_t out_is_device);
+
+/* Counter of the next sweep. */
+int sw_potts_get_sweep(sw_potts* h, uint32_t* t_out);
+
+/* Release the lattice (synchronises its stream). NULL is a no-op. */
+int sw_potts_destroy(sw_potts* h);
 
 /* Largest side accepted by sw_sweep_noalloc. */
 #define SW_NOALLOC_MAX_L 1024

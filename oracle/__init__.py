@@ -21,6 +21,9 @@ each function (what pins it, in tests/test_oracle_*.py):
                  transition matrix and 4x4 moments of the assign chain
   observe     -- closed forms of ordered, checkerboard and striped states
   histogram   -- against cluster sizes from scipy's labelling
+  potts_*     -- q = 2 equals the Ising assignment chain at twice beta (state 1
+                 <-> spin -1, E and M mapped); exact 2x2 q = 3 transition
+                 matrix (detailed balance); 3x3 q = 3 exact moments
   run         -- exact 2x2 transition matrix (detailed balance), 3x3 state
                  histogram vs Boltzmann, 4x4 exact moments, Kaufman's exact
                  finite-torus energy, Onsager-Yang magnetisation
@@ -88,6 +91,19 @@ def _load():
         lib.oracle_run.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                                    ctypes.c_int, P, P, P, P, ctypes.c_int]
         lib.oracle_run.restype = ctypes.c_int
+        lib.oracle_potts_threshold.argtypes = [ctypes.c_double]
+        lib.oracle_potts_threshold.restype = ctypes.c_uint32
+        lib.oracle_potts_init.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, P]
+        lib.oracle_potts_init.restype = None
+        lib.oracle_potts_assign.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, P, P]
+        lib.oracle_potts_assign.restype = None
+        lib.oracle_potts_apply.argtypes = [ctypes.c_int, P, P, P]
+        lib.oracle_potts_apply.restype = None
+        lib.oracle_potts_observe.argtypes = [ctypes.c_int, P, P, P]
+        lib.oracle_potts_observe.restype = None
+        lib.oracle_potts_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                         ctypes.c_uint32, ctypes.c_int, P, P, P]
+        lib.oracle_potts_run.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -226,3 +242,65 @@ def run(L: int, beta: float, seed: int, n: int, *, spins: np.ndarray | None = No
     if rc != 0:
         raise MemoryError("oracle_run: allocation failed")
     return s, E[:n], M[:n], (H[:n] if hist else None)
+
+
+# ------------------------------------------------------------ q-state Potts
+# §6's generalisation: H = -sum over edges of delta(s_i, s_j), states
+# 0..q-1 (int8); bonds between equal states with p = 1 - exp(-beta) (the
+# Ising bond draws C5 otherwise); each cluster assigned a state uniform in q
+# from word x0 of block (root, t, 3, 0) as floor(x0 q / 2^32).
+
+def _check_q(q: int):
+    if not (2 <= q <= 127):
+        raise ValueError("q must be in 2..127")
+
+
+def potts_threshold(beta: float) -> int:
+    return int(_load().oracle_potts_threshold(float(beta)))
+
+
+def potts_init(L: int, q: int, seed: int, cold: bool = False) -> np.ndarray:
+    _check_L(L)
+    _check_q(q)
+    s = np.zeros((L, L), dtype=np.int8)
+    _load().oracle_potts_init(L, q, seed, 1 if cold else 0, _ptr(s))
+    return s
+
+
+def potts_assign(L: int, q: int, lab: np.ndarray, seed: int, t: int) -> np.ndarray:
+    s = np.zeros((L, L), dtype=np.int8)
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    _load().oracle_potts_assign(L, q, seed, t & 0xffffffff, _ptr(lab), _ptr(s))
+    return s
+
+
+def potts_apply(L: int, lab: np.ndarray, state_of_root: np.ndarray) -> np.ndarray:
+    s = np.zeros((L, L), dtype=np.int8)
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    v = np.ascontiguousarray(state_of_root, dtype=np.uint8).reshape(-1)
+    _load().oracle_potts_apply(L, _ptr(lab), _ptr(v), _ptr(s))
+    return s
+
+
+def potts_observe(states: np.ndarray):
+    """(E, M): E = -(edges joining equal states), M = sites in state 0."""
+    s = np.ascontiguousarray(states, dtype=np.int8)
+    E = np.zeros(1, dtype=np.int64)
+    M = np.zeros(1, dtype=np.int64)
+    _load().oracle_potts_observe(s.shape[0], _ptr(s), _ptr(E), _ptr(M))
+    return int(E[0]), int(M[0])
+
+
+def potts_run(L: int, q: int, beta: float, seed: int, n: int, *, states: np.ndarray | None = None,
+              cold: bool = False, t0: int = 0):
+    """n Potts sweeps; returns (final states int8 [L, L], E int64 [n], M int64 [n])."""
+    _check_L(L)
+    _check_q(q)
+    if not (float(beta) >= 0.0) or np.isinf(beta):
+        raise ValueError("beta must be finite and >= 0")
+    s = potts_init(L, q, seed, cold) if states is None else np.array(states, dtype=np.int8, copy=True, order="C")
+    E = np.zeros(max(n, 1), dtype=np.int64)
+    M = np.zeros(max(n, 1), dtype=np.int64)
+    if _load().oracle_potts_run(L, q, float(beta), seed, t0 & 0xffffffff, n, _ptr(s), _ptr(E), _ptr(M)) != 0:
+        raise MemoryError("oracle_potts_run: allocation failed")
+    return s, E[:n], M[:n]

@@ -270,3 +270,91 @@ int oracle_run(int L, double beta, uint64_t seed, uint32_t t0, int n, int8_t* s,
     free(bonds); free(label); free(queue); free(count);
     return 0;
 }
+
+/* ======================================================= q-state Potts */
+/* The paper's §6 generalisation to the q-state Potts model, H = -sum over
+ * the 2N edges of delta(s_i, s_j), states 0..q-1 stored as int8. The SW
+ * rule bonds equal neighbours with probability 1 - exp(-beta); the bond
+ * draws (C5), BFS labels (C9) and oracle_bonds/oracle_labels are those of
+ * the Ising sweep; each cluster is assigned a new state uniform in q. For
+ * q = 2 and beta_Potts = 2 beta this chain is the Ising chain with the
+ * assignment rule, state 1 <-> spin -1. */
+
+/* thr = floor(2^32 * (1 - exp(-beta))), capped at 2^32 - 1. */
+uint32_t oracle_potts_threshold(double beta) {
+    if (!(beta >= 0.0) || isinf(beta)) return 0u;
+    double p = -expm1(-beta);
+    double scaled = floor(ldexp(p, 32));
+    if (scaled >= 4294967295.0) return 0xffffffffu;
+    return (uint32_t)scaled;
+}
+
+/* A uniform state in 0..q-1 from a 32-bit word: floor(x * q / 2^32). */
+static int8_t potts_state(uint32_t x, int q) {
+    return (int8_t)(((uint64_t)x * (uint64_t)q) >> 32);
+}
+
+/* Hot start: state from word x0 of block (i, 0, 2, 0); cold start: all 0. */
+void oracle_potts_init(int L, int q, uint64_t seed, int cold, int8_t* s) {
+    int64_t N = (int64_t)L * L;
+    for (int64_t i = 0; i < N; ++i) {
+        if (cold) { s[i] = 0; continue; }
+        uint32_t w[4];
+        philox_seeded(seed, (uint32_t)i, 0u, 2u, 0u, w);
+        s[i] = potts_state(w[0], q);
+    }
+}
+
+/* New states: the cluster rooted at r takes the state from word x0 of
+ * block (r, t, 3, 0). */
+void oracle_potts_assign(int L, int q, uint64_t seed, uint32_t t, const int32_t* label, int8_t* s) {
+    int64_t N = (int64_t)L * L;
+    for (int64_t i = 0; i < N; ++i) {
+        uint32_t w[4];
+        philox_seeded(seed, (uint32_t)label[i], t, 3u, 0u, w);
+        s[i] = potts_state(w[0], q);
+    }
+}
+
+/* Explicit new state per cluster, read at the root (exact-kernel tests). */
+void oracle_potts_apply(int L, const int32_t* label, const uint8_t* state_of_root, int8_t* s) {
+    int64_t N = (int64_t)L * L;
+    for (int64_t i = 0; i < N; ++i) s[i] = (int8_t)state_of_root[label[i]];
+}
+
+/* E = -(number of edges joining equal states), M = number of sites in state 0. */
+void oracle_potts_observe(int L, const int8_t* s, int64_t* E, int64_t* M) {
+    int64_t e = 0, m = 0;
+    for (int y = 0; y < L; ++y) {
+        for (int x = 0; x < L; ++x) {
+            int64_t i = (int64_t)y * L + x;
+            if (s[i] == s[(int64_t)y * L + (x + 1) % L]) e -= 1;
+            if (s[i] == s[(int64_t)((y + 1) % L) * L + x]) e -= 1;
+            if (s[i] == 0) m += 1;
+        }
+    }
+    *E = e;
+    *M = m;
+}
+
+int oracle_potts_run(int L, int q, double beta, uint64_t seed, uint32_t t0, int n, int8_t* s,
+                     int64_t* E_out, int64_t* M_out) {
+    int64_t N = (int64_t)L * L;
+    uint32_t thr = oracle_potts_threshold(beta);
+    uint8_t* bonds = (uint8_t*)malloc((size_t)N);
+    int32_t* label = (int32_t*)malloc((size_t)N * sizeof(int32_t));
+    int32_t* queue = (int32_t*)malloc((size_t)N * sizeof(int32_t));
+    if (!bonds || !label || !queue) {
+        free(bonds); free(label); free(queue);
+        return -1;
+    }
+    for (int k = 0; k < n; ++k) {
+        uint32_t t = t0 + (uint32_t)k;
+        oracle_bonds(L, seed, t, thr, s, bonds);
+        oracle_labels(L, bonds, label, queue);
+        oracle_potts_assign(L, q, seed, t, label, s);
+        oracle_potts_observe(L, s, &E_out[k], &M_out[k]);
+    }
+    free(bonds); free(label); free(queue);
+    return 0;
+}

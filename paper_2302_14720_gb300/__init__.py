@@ -49,6 +49,7 @@ SIGNATURES = {
     "sw_set_rule": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sw_histograms": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P]),
     "sw_labels": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "sw_labels_equivalence": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "sw_spins": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "sw_set_state": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_int32]),
     "sw_bonds": (ctypes.c_int, [_P, _P]),
@@ -73,6 +74,16 @@ SIGNATURES = {
     "sw_shape_info": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P]),
     "sw_tune_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
     "sw_last_error": (ctypes.c_char_p, []),
+    "sw_potts_threshold": (ctypes.c_uint32, [ctypes.c_double]),
+    "sw_potts_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64,
+                                       ctypes.c_int32, _P, ctypes.POINTER(_P)]),
+    "sw_potts_sweep": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sw_potts_observables": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "sw_potts_states": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "sw_potts_set_state": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_int32]),
+    "sw_potts_labels": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "sw_potts_get_sweep": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32)]),
+    "sw_potts_destroy": (ctypes.c_int, [_P]),
 }
 SW_NOALLOC_MAX_L = 1024
 
@@ -166,6 +177,18 @@ def sw_labels(h: int, L: int, out_device_ptr: int | None = None):
     out = np.zeros((L, L), np.int32)
     _check(_lib.sw_labels(h, _host_ptr(out), 0), "sw_labels")
     return out
+
+
+def sw_labels_equivalence(h: int, L: int, out=None):
+    """Labels by the paper's label-equivalence iteration; returns (labels, iterations).
+    With out a device pointer (int), the labels go there and None is returned for them."""
+    its = ctypes.c_int32(0)
+    if out is None:
+        lab = np.zeros((L, L), np.int32)
+        _check(_lib.sw_labels_equivalence(h, _host_ptr(lab), 0, ctypes.byref(its)), "sw_labels_equivalence")
+        return lab, its.value
+    _check(_lib.sw_labels_equivalence(h, ctypes.c_void_p(out), 1, ctypes.byref(its)), "sw_labels_equivalence")
+    return None, its.value
 
 
 def sw_spins(h: int, L: int, out_device_ptr: int | None = None):
@@ -346,6 +369,9 @@ class Lattice:
     def labels(self) -> np.ndarray:
         return sw_labels(self.h, self.L)
 
+    def labels_equivalence(self):
+        return sw_labels_equivalence(self.h, self.L)
+
     def bonds(self) -> np.ndarray:
         return sw_bonds(self.h, self.L)
 
@@ -355,6 +381,71 @@ class Lattice:
     def close(self) -> None:
         if self.h:
             sw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ------------------------------------------------------------ q-state Potts
+
+def sw_potts_threshold(beta: float) -> int:
+    return int(_lib.sw_potts_threshold(float(beta)))
+
+
+class Potts:
+    """Owning wrapper of one sw_potts handle (q-state Potts, states 0..q-1)."""
+
+    def __init__(self, L: int, q: int, beta: float, seed: int, init: int = SW_INIT_HOT, stream: int | None = None):
+        self.L, self.q = int(L), int(q)
+        h = ctypes.c_void_p()
+        _check(_lib.sw_potts_create(int(L), int(q), float(beta), int(seed) & 0xFFFFFFFFFFFFFFFF, int(init),
+                                    ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)), "sw_potts_create")
+        self.h = h.value
+
+    def sweep(self, n: int = 1) -> None:
+        _check(_lib.sw_potts_sweep(self.h, int(n)), "sw_potts_sweep")
+
+    @property
+    def t(self) -> int:
+        t = ctypes.c_uint32()
+        _check(_lib.sw_potts_get_sweep(self.h, ctypes.byref(t)), "sw_potts_get_sweep")
+        return t.value
+
+    def observables(self, first: int, count: int):
+        E = np.zeros(max(count, 0), np.int64)
+        M = np.zeros(max(count, 0), np.int64)
+        _check(_lib.sw_potts_observables(self.h, int(first), int(count), _host_ptr(E), _host_ptr(M)),
+               "sw_potts_observables")
+        return E, M
+
+    def states(self) -> np.ndarray:
+        out = np.zeros((self.L, self.L), np.int8)
+        _check(_lib.sw_potts_states(self.h, _host_ptr(out), 0), "sw_potts_states")
+        return out
+
+    def set_state(self, states, t: int) -> None:
+        a = np.ascontiguousarray(states, dtype=np.int8)
+        assert a.shape == (self.L, self.L)
+        _check(_lib.sw_potts_set_state(self.h, _host_ptr(a), int(t) & 0xFFFFFFFF, 0), "sw_potts_set_state")
+
+    def labels(self) -> np.ndarray:
+        out = np.zeros((self.L, self.L), np.int32)
+        _check(_lib.sw_potts_labels(self.h, _host_ptr(out), 0), "sw_potts_labels")
+        return out
+
+    def close(self) -> None:
+        if self.h:
+            _lib.sw_potts_destroy(self.h)
             self.h = None
 
     def __del__(self):

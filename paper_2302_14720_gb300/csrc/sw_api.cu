@@ -110,6 +110,8 @@ struct sw_lattice {
   int64_t* hist = nullptr;  // [cap][SW_HIST_WORDS]
   int32_t* label_buf = nullptr;
   uint8_t* bond_buf = nullptr;
+  int32_t* ref_buf = nullptr;  // label-equivalence references
+  int* le_flag = nullptr;
   int8_t* staging = nullptr;  // host sw_set_state lands here and is checked first
   int* check_flag = nullptr;
   // per-phase timing (sw_timing)
@@ -128,7 +130,8 @@ namespace {
 
 void free_all(sw_lattice* h) {
   void* ptrs[] = {h->spins, h->tb.tbits, h->tb.roots, h->tb.bmask, h->tb.nodes, h->tb.bslot, h->tb.bbits, h->tb.nslots, h->tb.err,
-                  h->csize, h->em, h->hist, h->label_buf, h->bond_buf, h->staging, h->check_flag};
+                  h->csize, h->em, h->hist, h->label_buf, h->bond_buf, h->ref_buf, h->le_flag, h->staging,
+                  h->check_flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& m : h->marks) {
@@ -529,6 +532,34 @@ int sw_timing_read(sw_lattice* h, double* ms_out, int64_t* launches_out) {
     if (launches_out) launches_out[k] = h->phase_launches[k];
   }
   return SW_OK;
+}
+
+int sw_labels_equivalence(sw_lattice* h, int32_t* out, int32_t out_is_device, int32_t* iterations) {
+  if (!h || !out) return fail(SW_EINVAL, "NULL argument");
+  const size_t N = (size_t)h->L * h->L;
+  if (!h->bond_buf) SW_CUDA(cudaMalloc(&h->bond_buf, N), "bond buffer");
+  if (!h->ref_buf) SW_CUDA(cudaMalloc(&h->ref_buf, N * sizeof(int32_t)), "reference buffer");
+  if (!h->le_flag) SW_CUDA(cudaMalloc(&h->le_flag, sizeof(int)), "iteration flag");
+  int32_t* dst = out;
+  if (!out_is_device) {
+    if (!h->label_buf) SW_CUDA(cudaMalloc(&h->label_buf, N * sizeof(int32_t)), "label buffer");
+    dst = h->label_buf;
+  }
+  sw::SweepArgs a = args_of(h);
+  a.em = nullptr;
+  a.hist = nullptr;
+  a.csize = nullptr;
+  SW_CUDA(sw::launch_phase1(h->shape, a, h->stream), "phase 1 launch");
+  SW_CUDA(sw::launch_export_bonds(h->shape, a, h->bond_buf, h->stream), "bond export launch");
+  int its = 0;
+  SW_CUDA(sw::run_label_equivalence(h->bond_buf, h->L, dst, h->ref_buf, h->le_flag, h->tb.err, 1 << 20, &its,
+                                    h->stream),
+          "label equivalence");
+  if (iterations) *iterations = its < 0 ? -its : its;
+  if (its < 0) return fail(SW_ETIMEOUT, "label equivalence did not converge within its iteration cap");
+  if (!out_is_device)
+    SW_CUDA(cudaMemcpyAsync(out, dst, N * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "labels copy");
+  return sync_and_check(h);
 }
 
 int sw_bonds(sw_lattice* h, uint8_t* out_host) {

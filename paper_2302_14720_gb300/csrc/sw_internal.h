@@ -142,6 +142,12 @@ struct SmallArgs {
   int* err;        // device error flag
 };
 cudaError_t launch_small(const SmallArgs& a, cudaStream_t st);
+
+// The paper's label-equivalence iteration (§2.3) over exported bonds
+// (uint8 per site, bit 0 east, bit 1 south); comparator only (sw_equiv.cu).
+// iterations: count run, negated if max_iter was reached first.
+cudaError_t run_label_equivalence(const uint8_t* bonds, int L, int32_t* lab, int32_t* ref, int* d_changed, int* err,
+                                  int max_iter, int* iterations, cudaStream_t st);
 // Debug: expand the stored bond bits into uint8 [L][L] (bit0 east, bit1 south).
 cudaError_t launch_export_bonds(int shape, const SweepArgs& a, uint8_t* out, cudaStream_t st);
 

@@ -163,10 +163,29 @@ __device__ __forceinline__ int find_final(const volatile uint16_t* par, int x) {
 // Lock-free union: the larger root is hung under the smaller one; a failed
 // minimum means another thread linked `a` first, and the loop carries on
 // with a's new parent. The cap only guards against corrupted memory.
+// Roots of a and b (as find_shared), the two paths walked side by side so
+// that their loads overlap.
+__device__ __forceinline__ void find_shared2(volatile uint16_t* par, int& a, int& b) {
+  for (;;) {
+    const int pa = par[a], pb = par[b];
+    const bool ra = pa == a, rb = pb == b;
+    if (ra && rb) return;
+    const int ga = ra ? a : par[pa];
+    const int gb = rb ? b : par[pb];
+    if (!ra) {
+      if (ga != pa) par[a] = (uint16_t)ga;
+      a = ga;
+    }
+    if (!rb) {
+      if (gb != pb) par[b] = (uint16_t)gb;
+      b = gb;
+    }
+  }
+}
+
 __device__ void unite_shared(uint16_t* par, int a, int b, int* err) {
   for (int it = 0; it < kUnionCap; ++it) {
-    a = find_shared(par, a);
-    b = find_shared(par, b);
+    find_shared2(par, a, b);
     if (a == b) return;
     if (a < b) {
       const int tmp = a;
@@ -580,20 +599,67 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
 
   // ---- tile-local clusters (§2.3)
   strip_scan<WPR, H>(par, e_int, d_int, wmask, y0r, nv, w);
+  // the roots of my strip's components: only these are ever linked below
+  uint32_t sroot[H];
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    sroot[r] = 0u;
+    if (r >= nv) continue;
+    const int base = (y0r + r) * TW + 32 * w;
+    uint32_t R = ~(e_int[r] << 1) & wmask;
+    while (R) {
+      const int b = __ffs(R) - 1;
+      R &= R - 1;
+      if (par[base + b] == base + b) sroot[r] |= 1u << b;
+    }
+  }
   __syncthreads();
   strip_joins<WPR, TH, H, PL>(par, e_int, wmask, y0r, nv, w, k, s_eint, s_dint, a.tb.err);
   __syncthreads();
 
-  // every run start of my strip points at its tile root
+  // the joins leave chains of strip roots (a strip's root hung under the
+  // root of the strip above, and so on); walking them first from the strip
+  // roots, halving as we go, keeps every later walk short
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    const int base = (y0r + r) * TW + 32 * w;
+    uint32_t R = sroot[r];
+    while (R) {
+      const int b = __ffs(R) - 1;
+      R &= R - 1;
+      find_shared(par, base + b);
+    }
+  }
+  __syncthreads();
+
+  // every run start of my strip points at its tile root. Most run starts
+  // are at most two hops from it, so they are taken four at a time with
+  // their two hops loaded side by side; longer paths finish one by one.
 #pragma unroll
   for (int r = 0; r < H; ++r) {
     if (r >= nv) break;
     const int base = (y0r + r) * TW + 32 * w;
     uint32_t R = ~(e_int[r] << 1) & wmask;
     while (R) {
-      const int b = __ffs(R) - 1;
-      R &= R - 1;
-      par[base + b] = (uint16_t)find_final(par, base + b);
+      constexpr int G = 4;
+      int x[G], p[G], pp[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        x[q] = -1;
+        if (R) {
+          x[q] = base + __ffs(R) - 1;
+          R &= R - 1;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < G; ++q) p[q] = x[q] >= 0 ? par[x[q]] : 0;
+#pragma unroll
+      for (int q = 0; q < G; ++q) pp[q] = x[q] >= 0 ? par[p[q]] : 0;
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        if (x[q] < 0) continue;
+        par[x[q]] = (uint16_t)(pp[q] == p[q] ? p[q] : find_final(par, pp[q]));
+      }
     }
   }
   __syncthreads();
