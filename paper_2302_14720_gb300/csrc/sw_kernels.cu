@@ -111,15 +111,11 @@ __device__ __forceinline__ void store_spin_bits(int8_t* p, uint32_t bits, int nb
 
 // Replace the 16-bit entry at p by v if it is larger; returns the old entry.
 __device__ __forceinline__ uint32_t atomic_min_u16(uint16_t* p, uint32_t v) {
-  unsigned int* w = reinterpret_cast<unsigned int*>(reinterpret_cast<uintptr_t>(p) & ~uintptr_t(3));
-  const int sh = (reinterpret_cast<uintptr_t>(p) & 2u) ? 16 : 0;
-  unsigned int old = *reinterpret_cast<volatile unsigned int*>(w);
+  unsigned short old = *reinterpret_cast<volatile unsigned short*>(p);
   for (;;) {
-    const uint32_t cur = (old >> sh) & 0xFFFFu;
-    if (cur <= v) return cur;
-    const unsigned int nw = (old & ~(0xFFFFu << sh)) | (v << sh);
-    const unsigned int seen = atomicCAS(w, old, nw);
-    if (seen == old) return cur;
+    if (old <= v) return old;
+    const unsigned short seen = atomicCAS(reinterpret_cast<unsigned short*>(p), old, (unsigned short)v);
+    if (seen == old) return old;
     old = seen;
   }
 }
@@ -356,7 +352,7 @@ __device__ __forceinline__ void strip_scan(uint16_t* par, const uint32_t (&e_int
 template <int WPR, int TH, int H, int PL>
 __device__ __forceinline__ void strip_joins(uint16_t* par, const uint32_t (&e_int)[H], uint32_t vmask, int y0r,
                                             int nv, int w, int k, const uint32_t (*s_eint)[WPR],
-                                            const uint32_t (*s_dint)[WPR], int* err) {
+                                            const uint32_t (*s_dint)[WPR], uint32_t* q, int* err) {
   constexpr int TW = 32 * WPR;
   // The first PL rounds merge strips pairwise without atomics: in round st
   // the boundary above strip k is joined when k % (2 st) == st, by k's
@@ -380,23 +376,54 @@ __device__ __forceinline__ void strip_joins(uint16_t* par, const uint32_t (&e_in
     }
     __syncthreads();
   }
+  // The remaining joins are atomic unions. The lanes of a warp walk their
+  // bonds in step and queue the pairs to unite (q: the warp's 64 entries,
+  // both ends packed in 16 bits each); the queue is taken 32 pairs at a
+  // time, so every lane unites instead of idling behind the busiest one.
+  const int lane = threadIdx.x & 31;
+  int qh = 0, qn = 0;  // the same in every lane of the warp
+  auto push = [&](bool have, uint32_t pair) {
+    const uint32_t m = __ballot_sync(0xffffffffu, have);
+    if (have) q[(qh + qn + __popc(m & ((1u << lane) - 1u))) & 63] = pair;
+    qn += __popc(m);
+    __syncwarp();
+    if (qn >= 32) {
+      const uint32_t v = q[(qh + lane) & 63];
+      unite_shared(par, (int)(v & 0xFFFFu), (int)(v >> 16), err);
+      qh += 32;
+      qn -= 32;
+      __syncwarp();
+    }
+  };
+  uint32_t need = 0u, Rp = 0u, Rc = 0u;
+  int bp = 0, bc = 0;
   if (y0r > 0 && nv > 0 && (k % (1 << PL)) == 0) {
     const uint32_t ep = s_eint[y0r - 1][w], du = s_dint[y0r - 1][w], ec = e_int[0];
-    const uint32_t Rp = ~(ep << 1) & vmask, Rc = ~(ec << 1) & vmask;
-    uint32_t need = du & ~((du & ep & ec) << 1);
-    const int bp = (y0r - 1) * TW + 32 * w, bc = bp + TW;
-    while (need) {
+    Rp = ~(ep << 1) & vmask;
+    Rc = ~(ec << 1) & vmask;
+    need = du & ~((du & ep & ec) << 1);
+    bp = (y0r - 1) * TW + 32 * w;
+    bc = bp + TW;
+  }
+  while (__any_sync(0xffffffffu, need != 0u)) {
+    const bool have = need != 0u;
+    uint32_t pair = 0u;
+    if (have) {
       const int j = __ffs(need) - 1;
       need &= need - 1;
-      unite_shared(par, bp + run_start(Rp, j), bc + run_start(Rc, j), err);
+      pair = (uint32_t)(bp + run_start(Rp, j)) | ((uint32_t)(bc + run_start(Rc, j)) << 16);
     }
+    push(have, pair);
   }
 #pragma unroll
   for (int r = 0; r < H; ++r) {
-    if (r < nv && ((e_int[r] >> 31) & 1u)) {
-      const int base = (y0r + r) * TW + 32 * w;
-      unite_shared(par, base + run_start(~(e_int[r] << 1), 31), base + 32, err);
-    }
+    const bool have = r < nv && ((e_int[r] >> 31) & 1u);
+    const int base = (y0r + r) * TW + 32 * w;
+    push(have, have ? (uint32_t)(base + run_start(~(e_int[r] << 1), 31)) | ((uint32_t)(base + 32) << 16) : 0u);
+  }
+  if (lane < qn) {
+    const uint32_t v = q[(qh + lane) & 63];
+    unite_shared(par, (int)(v & 0xFFFFu), (int)(v >> 16), err);
   }
 }
 
@@ -614,7 +641,9 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
     }
   }
   __syncthreads();
-  strip_joins<WPR, TH, H, PL>(par, e_int, wmask, y0r, nv, w, k, s_eint, s_dint, a.tb.err);
+  // s_pre is free until the border slots: it holds the warps' join queues
+  static_assert((NT / 32) * 64 <= RW, "join queues fit in s_pre");
+  strip_joins<WPR, TH, H, PL>(par, e_int, wmask, y0r, nv, w, k, s_eint, s_dint, s_pre + (tid >> 5) * 64, a.tb.err);
   __syncthreads();
 
   // the joins leave chains of strip roots (a strip's root hung under the
@@ -823,6 +852,7 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
   __shared__ uint32_t s_pre[RW];
   __shared__ uint32_t s_wsum[33];
   __shared__ uint32_t s_flip[RW];                  // decision bit of every root (flip, or new sign)
+  __shared__ uint16_t s_rootq[NT / 32][64];        // inner roots waiting for their draw
   __shared__ uint32_t s_snew[TH][WPR];
   __shared__ int s_slotval[MS];                    // flip bit (flip modes) or canonical label (labels mode)
   __shared__ uint32_t s_slotroot[HIST ? MS : 1];
@@ -880,32 +910,56 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
   __syncthreads();
 
   // ---- decision bit of every root of my strip: border roots from their slot,
-  // inner roots from one Philox block each (C6, or the assignment rule)
+  // inner roots from one Philox block each (C6, or the assignment rule).
+  // The lanes of a warp walk their run starts in step and queue their inner
+  // roots; the queue is drawn 32 roots at a time, so every lane draws.
   if (!LABELS) {
+    const int warp = tid >> 5;
+    uint16_t* q = s_rootq[warp];
+    int qh = 0, qn = 0;  // the same in every lane of the warp
+    auto draw = [&](int x) {
+      const uint32_t key = (uint32_t)(P.y0 + x / TW) * (uint32_t)L + (uint32_t)(P.x0 + x % TW);
+      if (decision_bit(key, a.t, a.ks, a.rule)) atomicOr(&s_flip[x >> 5], 1u << (x & 31));
+    };
+#pragma unroll
+    for (int r = 0; r < H; ++r) s_flip[(y0r + r) * WPR + w] = 0u;
+    __syncwarp();
 #pragma unroll
     for (int r = 0; r < H; ++r) {
       const int y = y0r + r, base = y * TW + 32 * w, rw = y * WPR + w;
       uint32_t fl = 0;
-      if (r < nv) {
-        uint32_t R = ~(e_int[r] << 1) & wmask;
-        const uint32_t bm = s_bmask[rw];
-        while (R) {
+      uint32_t R = r < nv ? (~(e_int[r] << 1) & wmask) : 0u;
+      const uint32_t bm = s_bmask[rw];
+      while (__any_sync(0xffffffffu, R != 0u)) {
+        bool inner = false;
+        int x = 0;
+        if (R) {
           const int b = __ffs(R) - 1;
           R &= R - 1;
-          if (par[base + b] != base + b) continue;
-          uint32_t f;
-          if ((bm >> b) & 1u) {
-            const int sl = slot_of(s_bmask, s_pre, base + b);
-            f = sl < nsl ? (uint32_t)s_slotval[sl] : 0u;
-          } else {
-            f = decision_bit((uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w + b), a.t, a.ks,
-                             a.rule);
+          x = base + b;
+          if (par[x] == x) {
+            if ((bm >> b) & 1u) {
+              const int sl = slot_of(s_bmask, s_pre, x);
+              fl |= (sl < nsl ? (uint32_t)s_slotval[sl] : 0u) << b;
+            } else {
+              inner = true;
+            }
           }
-          fl |= f << b;
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, inner);
+        if (inner) q[(qh + qn + __popc(m & ((1u << lane) - 1u))) & 63] = (uint16_t)x;
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+          draw(q[(qh + lane) & 63]);
+          qh += 32;
+          qn -= 32;
+          __syncwarp();
         }
       }
-      s_flip[rw] = fl;
+      if (fl) atomicOr(&s_flip[rw], fl);
     }
+    if (lane < qn) draw(q[(qh + lane) & 63]);
     __syncthreads();
   }
 

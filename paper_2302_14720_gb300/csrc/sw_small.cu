@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_sweep_kernel(const SmallA
   extern __shared__ __align__(16) uint32_t smem[];
   constexpr int NT = kSmallThreads, NW = NT / 32;
   __shared__ long long s_red[2][NW];
+  __shared__ uint16_t s_rootq[NW][64];  // roots waiting for their draw
   const int L = a.L, N = L * L, WPL = (L + 31) >> 5, RWN = L * WPL, DW = (N + 31) >> 5;
   uint32_t* s_spin = smem;       // [RWN] sign bits (1 = -1)
   uint32_t* s_e = s_spin + RWN;  // [RWN] east bonds
@@ -138,15 +139,39 @@ __global__ void __launch_bounds__(kSmallThreads) small_sweep_kernel(const SmallA
     }
     __syncthreads();
 
-    // ---- every site points at its root; roots draw their decision (C6 / C6b)
-    for (int i = tid; i < N; i += NT) {
-      int r = i, p = par[r];
-      while (p != r) {
-        r = p;
-        p = par[r];
+    // ---- every site points at its root; roots draw their decision (C6 /
+    // C6b), queued per warp and drawn 32 at a time so that every lane draws
+    {
+      uint16_t* q = s_rootq[warp];
+      int qh = 0, qn = 0;  // the same in every lane of the warp
+      for (int i0 = warp * 32; i0 < N; i0 += NT) {
+        const int i = i0 + lane;
+        bool isroot = false;
+        if (i < N) {
+          int r = i, p = par[r];
+          while (p != r) {
+            r = p;
+            p = par[r];
+          }
+          par[i] = (uint16_t)r;  // concurrent stores all write roots
+          isroot = r == i;
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, isroot);
+        if (isroot) q[(qh + qn + __popc(m & ((1u << lane) - 1u))) & 63] = (uint16_t)i;
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+          const int x = q[(qh + lane) & 63];
+          if (decision_bit((uint32_t)x, t, a.ks, a.rule)) atomicOr(&s_dec[x >> 5], 1u << (x & 31));
+          qh += 32;
+          qn -= 32;
+          __syncwarp();
+        }
       }
-      par[i] = (uint16_t)r;  // concurrent stores all write roots
-      if (r == i && decision_bit((uint32_t)i, t, a.ks, a.rule)) atomicOr(&s_dec[i >> 5], 1u << (i & 31));
+      if (lane < qn) {
+        const int x = q[(qh + lane) & 63];
+        if (decision_bit((uint32_t)x, t, a.ks, a.rule)) atomicOr(&s_dec[x >> 5], 1u << (x & 31));
+      }
     }
     __syncthreads();
 
