@@ -55,11 +55,11 @@ RW = (TW // 32) * TH  # 32-site row-words per tile
 # (8 bytes per border component) are data dependent and not counted.
 PHASE_BYTES_PER_TILE = {
     # spins + halo in; spin/east/south masks, 16-bit tile roots, border-root
-    # masks, border slots, tile bits, slot count out
-    0: (TW * TH + TH + TW) + (3 * RW * 4 + 2 * TW * TH + 4 * RW + 2 * NB + 4 * BBW + 4),
-    # spin/east masks, roots, border-root masks, slot count, tile bits,
-    # neighbours' halo slots in; spins out
-    2: (2 * RW * 4 + 2 * TW * TH + 4 * RW + 4 + 4 * BBW + 2 * (TH + TW)) + TW * TH,
+    # and root masks, border slots, tile bits, slot count out
+    0: (TW * TH + TH + TW) + (3 * RW * 4 + 2 * TW * TH + 2 * 4 * RW + 2 * NB + 4 * BBW + 4),
+    # spin/east masks, roots, border-root and root masks, slot count, tile
+    # bits, neighbours' halo slots in; spins out
+    2: (2 * RW * 4 + 2 * TW * TH + 2 * 4 * RW + 4 + 4 * BBW + 2 * (TH + TW)) + TW * TH,
 }
 PHASE_NAMES = {0: "phase1_bonds_tile_ccl", 1: "phase2_merge_resolve", 2: "phase3_flip_em", 3: "phase4_hist"}
 SWEEP_MODEL_BYTES_PER_SITE = 10  # read spins, write+read int32 labels, write spins

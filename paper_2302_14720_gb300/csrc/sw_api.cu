@@ -129,7 +129,7 @@ struct sw_lattice {
 namespace {
 
 void free_all(sw_lattice* h) {
-  void* ptrs[] = {h->spins, h->tb.tbits, h->tb.roots, h->tb.bmask, h->tb.nodes, h->tb.bslot, h->tb.bbits, h->tb.nslots, h->tb.err,
+  void* ptrs[] = {h->spins, h->tb.tbits, h->tb.roots, h->tb.bmask, h->tb.rbits, h->tb.nodes, h->tb.bslot, h->tb.bbits, h->tb.nslots, h->tb.err,
                   h->csize, h->em, h->hist, h->label_buf, h->bond_buf, h->ref_buf, h->le_flag, h->staging,
                   h->check_flag};
   for (void* p : ptrs)
@@ -305,6 +305,7 @@ int sw_create(int32_t L, double beta, uint64_t seed, int32_t init, void* stream,
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.tbits, ntiles * 3 * ts.row_words() * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.roots, ntiles * ts.sites() * sizeof(uint16_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.bmask, ntiles * ts.row_words() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.rbits, ntiles * ts.row_words() * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.nodes, ntiles * ts.max_slots() * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.bslot, ntiles * ts.boundary_sites() * sizeof(uint16_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.bbits, ntiles * ts.bbits_words() * sizeof(uint32_t));

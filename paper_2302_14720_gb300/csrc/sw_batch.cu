@@ -48,7 +48,7 @@ uint32_t thr_of(double beta) {
 }
 
 void free_replica(Replica& r) {
-  void* ptrs[] = {r.spins, r.tb.tbits, r.tb.roots, r.tb.bmask, r.tb.nodes, r.tb.bslot, r.tb.bbits, r.tb.nslots, r.em};
+  void* ptrs[] = {r.spins, r.tb.tbits, r.tb.roots, r.tb.bmask, r.tb.rbits, r.tb.nodes, r.tb.bslot, r.tb.bbits, r.tb.nslots, r.em};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   r = Replica{};
@@ -206,7 +206,7 @@ int grow_trace(Replica& r, int64_t needed, cudaStream_t st) {
 int64_t replica_bytes(const sw::TileShape& ts, int L, int64_t cap) {
   const int64_t nt = (int64_t)((L + ts.tw() - 1) / ts.tw()) * ((L + ts.th - 1) / ts.th);
   return (int64_t)L * L +
-         nt * (3 * ts.row_words() * 4 + ts.sites() * 2 + ts.row_words() * 4 + ts.max_slots() * 8 +
+         nt * (3 * ts.row_words() * 4 + ts.sites() * 2 + 2 * ts.row_words() * 4 + ts.max_slots() * 8 +
                ts.boundary_sites() * 2 + ts.bbits_words() * 4 + 4) +
          cap * 16;
 }
@@ -293,6 +293,7 @@ int sw_batch_add(sw_batch* b, int32_t L, double beta, uint64_t seed, int32_t ini
   if (e == cudaSuccess) e = cudaMalloc(&r.tb.tbits, nt * 3 * ts.row_words() * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&r.tb.roots, nt * ts.sites() * sizeof(uint16_t));
   if (e == cudaSuccess) e = cudaMalloc(&r.tb.bmask, nt * ts.row_words() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&r.tb.rbits, nt * ts.row_words() * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&r.tb.nodes, nt * ts.max_slots() * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&r.tb.bslot, nt * ts.boundary_sites() * sizeof(uint16_t));
   if (e == cudaSuccess) e = cudaMalloc(&r.tb.bbits, nt * ts.bbits_words() * sizeof(uint32_t));

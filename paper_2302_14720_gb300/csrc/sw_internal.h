@@ -54,6 +54,7 @@ struct TileBuffers {
   uint32_t* tbits;   // [ntiles][3][row_words]: spin bits, east-bond bits, south-bond bits per row-word
   uint16_t* roots;   // [ntiles][sites]: tile-local root of every run start (phase 1 -> phase 3)
   uint32_t* bmask;   // [ntiles][row_words]: bit set at every tile root that touches the tile border
+  uint32_t* rbits;   // [ntiles][row_words]: bit set at every tile root
   uint64_t* nodes;   // [ntiles * max_slots]: global union-find, (key << 32) | parent node
   uint16_t* bslot;   // [ntiles][boundary_sites]: slot of each boundary site (left, right, top, bottom)
   uint32_t* bbits;   // [ntiles][bbits_words]: E-out bonds, S-out bonds, east halo spins, south halo spins

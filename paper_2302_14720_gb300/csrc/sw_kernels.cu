@@ -664,9 +664,11 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
   // every run start of my strip points at its tile root. Most run starts
   // are at most two hops from it, so they are taken four at a time with
   // their two hops loaded side by side; longer paths finish one by one.
+  uint32_t rootbits[H];  // run starts that are tile roots
 #pragma unroll
   for (int r = 0; r < H; ++r) {
-    if (r >= nv) break;
+    rootbits[r] = 0u;
+    if (r >= nv) continue;
     const int base = (y0r + r) * TW + 32 * w;
     uint32_t R = ~(e_int[r] << 1) & wmask;
     while (R) {
@@ -687,6 +689,7 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
 #pragma unroll
       for (int q = 0; q < G; ++q) {
         if (x[q] < 0) continue;
+        if (p[q] == x[q]) rootbits[r] |= 1u << (x[q] - base);
         par[x[q]] = (uint16_t)(pp[q] == p[q] ? p[q] : find_final(par, pp[q]));
       }
     }
@@ -741,6 +744,7 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
 #pragma unroll
       for (int q = 0; q < 4; ++q) dst[q] = src[q];
       bm[(y0r + r) * WPR + w] = s_bmask[(y0r + r) * WPR + w];
+      a.tb.rbits[(size_t)P.tile * RW + (y0r + r) * WPR + w] = rootbits[r];
     }
   }
   for (int i = tid; i < BBW; i += NT) a.tb.bbits[(size_t)P.tile * BBW + i] = s_bb[i];
@@ -852,7 +856,6 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
   __shared__ uint32_t s_pre[RW];
   __shared__ uint32_t s_wsum[33];
   __shared__ uint32_t s_flip[RW];                  // decision bit of every root (flip, or new sign)
-  __shared__ uint16_t s_rootq[NT / 32][64];        // inner roots waiting for their draw
   __shared__ uint32_t s_snew[TH][WPR];
   __shared__ int s_slotval[MS];                    // flip bit (flip modes) or canonical label (labels mode)
   __shared__ uint32_t s_slotroot[HIST ? MS : 1];
@@ -910,56 +913,63 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
   __syncthreads();
 
   // ---- decision bit of every root of my strip: border roots from their slot,
-  // inner roots from one Philox block each (C6, or the assignment rule).
-  // The lanes of a warp walk their run starts in step and queue their inner
-  // roots; the queue is drawn 32 roots at a time, so every lane draws.
+  // the others from one Philox block each (C6, or the assignment rule).
+  // Phase 1 marked the roots. The lanes of a warp walk their inner roots in
+  // step and queue them (in s_snew, free until the new spins); the queue is
+  // drawn 64 roots at a time, two independent draws per lane.
   if (!LABELS) {
     const int warp = tid >> 5;
-    uint16_t* q = s_rootq[warp];
+    constexpr int QC = 128;  // queue entries per warp
+    static_assert((NT / 32) * QC <= 2 * TH * WPR, "root queues fit in s_snew");
+    uint16_t* q = reinterpret_cast<uint16_t*>(&s_snew[0][0]) + warp * QC;
     int qh = 0, qn = 0;  // the same in every lane of the warp
     auto draw = [&](int x) {
       const uint32_t key = (uint32_t)(P.y0 + x / TW) * (uint32_t)L + (uint32_t)(P.x0 + x % TW);
-      if (decision_bit(key, a.t, a.ks, a.rule)) atomicOr(&s_flip[x >> 5], 1u << (x & 31));
+      return decision_bit(key, a.t, a.ks, a.rule);
     };
+    const uint32_t* grb = a.tb.rbits + (size_t)P.tile * RW;
 #pragma unroll
     for (int r = 0; r < H; ++r) s_flip[(y0r + r) * WPR + w] = 0u;
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < H; ++r) {
       const int y = y0r + r, base = y * TW + 32 * w, rw = y * WPR + w;
-      uint32_t fl = 0;
-      uint32_t R = r < nv ? (~(e_int[r] << 1) & wmask) : 0u;
       const uint32_t bm = s_bmask[rw];
-      while (__any_sync(0xffffffffu, R != 0u)) {
-        bool inner = false;
+      uint32_t inner = r < nv ? grb[rw] & ~bm : 0u;
+      uint32_t fl = 0, B = r < nv ? bm : 0u;
+      while (B) {
+        const int b = __ffs(B) - 1;
+        B &= B - 1;
+        const int sl = slot_of(s_bmask, s_pre, base + b);
+        fl |= (sl < nsl ? (uint32_t)s_slotval[sl] : 0u) << b;
+      }
+      if (fl) atomicOr(&s_flip[rw], fl);
+      while (__any_sync(0xffffffffu, inner != 0u)) {
+        const bool have = inner != 0u;
         int x = 0;
-        if (R) {
-          const int b = __ffs(R) - 1;
-          R &= R - 1;
-          x = base + b;
-          if (par[x] == x) {
-            if ((bm >> b) & 1u) {
-              const int sl = slot_of(s_bmask, s_pre, x);
-              fl |= (sl < nsl ? (uint32_t)s_slotval[sl] : 0u) << b;
-            } else {
-              inner = true;
-            }
-          }
+        if (have) {
+          x = base + __ffs(inner) - 1;
+          inner &= inner - 1;
         }
-        const uint32_t m = __ballot_sync(0xffffffffu, inner);
-        if (inner) q[(qh + qn + __popc(m & ((1u << lane) - 1u))) & 63] = (uint16_t)x;
+        const uint32_t m = __ballot_sync(0xffffffffu, have);
+        if (have) q[(qh + qn + __popc(m & ((1u << lane) - 1u))) & (QC - 1)] = (uint16_t)x;
         qn += __popc(m);
         __syncwarp();
-        if (qn >= 32) {
-          draw(q[(qh + lane) & 63]);
-          qh += 32;
-          qn -= 32;
+        if (qn >= 64) {
+          const int x0 = q[(qh + lane) & (QC - 1)], x1 = q[(qh + 32 + lane) & (QC - 1)];
+          const uint32_t f0 = draw(x0), f1 = draw(x1);
+          if (f0) atomicOr(&s_flip[x0 >> 5], 1u << (x0 & 31));
+          if (f1) atomicOr(&s_flip[x1 >> 5], 1u << (x1 & 31));
+          qh += 64;
+          qn -= 64;
           __syncwarp();
         }
       }
-      if (fl) atomicOr(&s_flip[rw], fl);
     }
-    if (lane < qn) draw(q[(qh + lane) & 63]);
+    for (int k2 = lane; k2 < qn; k2 += 32) {
+      const int x = q[(qh + k2) & (QC - 1)];
+      if (draw(x)) atomicOr(&s_flip[x >> 5], 1u << (x & 31));
+    }
     __syncthreads();
   }
 

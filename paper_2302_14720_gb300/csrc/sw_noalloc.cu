@@ -32,7 +32,7 @@ constexpr int kNoallocShape = 6;  // 128 x 64 tiles, 2-row strips, as sw_sweep u
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct ScratchLayout {
-  size_t tbits, roots, bmask, nodes, bslot, bbits, nslots, total;
+  size_t tbits, roots, bmask, rbits, nodes, bslot, bbits, nslots, total;
 };
 
 // Buffer sizes of the tile pipeline (as sw_create allocates them) for side L;
@@ -49,7 +49,8 @@ constexpr ScratchLayout layout_for(int L) {
   s.tbits = 0;
   s.roots = s.tbits + align256(ntiles * 3 * threads * sizeof(uint32_t));
   s.bmask = s.roots + align256(ntiles * (size_t)tw * th * sizeof(uint16_t));
-  s.nodes = s.bmask + align256(ntiles * threads * sizeof(uint32_t));
+  s.rbits = s.bmask + align256(ntiles * threads * sizeof(uint32_t));
+  s.nodes = s.rbits + align256(ntiles * threads * sizeof(uint32_t));
   s.bslot = s.nodes + align256(ntiles * slots * sizeof(uint64_t));
   s.bbits = s.bslot + align256(ntiles * border * sizeof(uint16_t));
   s.nslots = s.bbits + align256(ntiles * bbits * sizeof(uint32_t));
@@ -136,6 +137,7 @@ extern "C" int sw_sweep_noalloc(int8_t* spins, int32_t L, double beta, uint64_t 
   a.tb.tbits = reinterpret_cast<uint32_t*>(base + lay.tbits);
   a.tb.roots = reinterpret_cast<uint16_t*>(base + lay.roots);
   a.tb.bmask = reinterpret_cast<uint32_t*>(base + lay.bmask);
+  a.tb.rbits = reinterpret_cast<uint32_t*>(base + lay.rbits);
   a.tb.nodes = reinterpret_cast<uint64_t*>(base + lay.nodes);
   a.tb.bslot = reinterpret_cast<uint16_t*>(base + lay.bslot);
   a.tb.bbits = reinterpret_cast<uint32_t*>(base + lay.bbits);
