@@ -421,6 +421,17 @@ def measure_other_configs(sw, torch, stream, flush):
         ms = timed_sweeps(torch, stream, lambda: pt.sweep(n), n)
         pt.observables(10, n)
     out["potts_q3_L1024_betac"] = {"su_s": 1024 * 1024 * n / (ms / 1e3), "us_per_sweep": 1e3 * ms / n, "sweeps": n}
+    # O(4) phi^4 multicluster updates at the paper's kappa = 0.304 (§5's
+    # second table: L = 16..28, 10^4 updates)
+    out["phi4_kappa0.304"] = {}
+    for Lp in (16, 28):
+        with sw.Phi4(Lp, 0.304, 6, stream=stream.cuda_stream) as f4:
+            f4.sweep(5)
+            n4 = 200
+            ms4 = timed_sweeps(torch, stream, lambda: f4.sweep(n4), n4)
+            f4.observables(5, n4)
+        out["phi4_kappa0.304"][f"L{Lp}"] = {"ms_per_update": ms4 / n4, "site_updates_s": Lp**4 * n4 / (ms4 / 1e3),
+                                            "updates": n4, "minutes_per_1e4_updates": ms4 / n4 * 1e4 / 6e4}
     return out
 
 

@@ -324,6 +324,65 @@ int sw_potts_get_sweep(sw_potts* h, uint32_t* t_out);
 /* Release the lattice (synchronises its stream). NULL is a no-op. */
 int sw_potts_destroy(sw_potts* h);
 
+/* ---------------------------------------------------------------------------
+ * O(4) phi^4 theory in four dimensions: the multicluster update (§3, Eqs. 2
+ * and 3)
+ * ---------------------------------------------------------------------------
+ *  O1  Lattice L^4, periodic, site x = x0 + L (x1 + L (x2 + L x3)); each
+ *      site owns its 4 edges to x + e_mu. Field phi_x in R^4, binary64,
+ *      stored [N][4].
+ *  O2  Hot start: component a of phi_x = (w_a + 0.5) 2^-31 - 1, w_a the
+ *      words of Philox block (x, 0, 7, 0); cold start phi_x = (1, 0, 0, 0).
+ *  O3  Direction r of update t, uniform on the unit 3-sphere: attempts
+ *      k = 0, 1, ...: v_a = (w_a + 0.5) 2^-31 - 1 from block (k, t, 5, 0),
+ *      s = fma(v3, v3, fma(v2, v2, fma(v1, v1, v0 * v0))); the first attempt
+ *      with 2^-20 < s <= 1 gives r_a = v_a / sqrt(s).
+ *  O4  Projection a_x = fma(phi3, r3, fma(phi2, r2, fma(phi1, r1, phi0 *
+ *      r0))). Edge (x, mu), y = x + e_mu, bonds iff q = a_x a_y > 0 and
+ *      (double) w_mu < (1 - e) 2^32 with e = e^{-(4 kappa) q} (Eq. 2), w_mu =
+ *      word mu of block (x, t, 4, 0). e is computed by the library's own
+ *      exponential (Cody-Waite reduction with a 32-bit head of ln 2, Taylor
+ *      series to degree 14 with fused multiply-adds, 0 for arguments above
+ *      40), so the decisions are reproducible bit for bit.
+ *  O5  Clusters: labels C9. The cluster rooted at r is flipped iff bit 31 of
+ *      word 0 of block (r, t, 6, 0); a flipped site's component a becomes
+ *      fma(-2 a_x, r_a, phi_a) (Eq. 3: reflection in the hyperplane
+ *      orthogonal to r).
+ *  Observables per update, binary64: E = sum over the 4N edges of
+ *  phi_x . phi_{x+mu}, M = sum_x phi_x (4 components). They are reduced in
+ *  parallel, so they match a serial sum to rounding, not bit for bit; the
+ *  field itself is bit-exact.
+ * --------------------------------------------------------------------------- */
+typedef struct sw_phi4 sw_phi4;
+
+/* Direction O3 of update t. r_out: 4 doubles. */
+int sw_phi4_direction(uint64_t seed, uint32_t t, double* r_out);
+
+/* New field on an L^4 torus (2 <= L, L^4 < 2^31), hopping coupling kappa
+ * (finite, >= 0), start O2. */
+int sw_phi4_create(int32_t L, double kappa, uint64_t seed, int32_t init, void* stream, sw_phi4** out);
+
+/* n >= 0 multicluster updates with counters t .. t+n-1. */
+int sw_phi4_sweep(sw_phi4* h, int32_t n);
+
+/* E_host[count] and M_host[count][4] of updates [first, first+count). */
+int sw_phi4_observables(sw_phi4* h, int64_t first, int64_t count, double* E_host, double* M_host);
+
+/* The field, double [N][4], host (synchronises) or device. */
+int sw_phi4_field(sw_phi4* h, double* out, int32_t out_is_device);
+
+/* Replace the field (host or device double [N][4]) and set the counter to t. */
+int sw_phi4_set_field(sw_phi4* h, const double* in, uint32_t t, int32_t in_is_device);
+
+/* Labels C9 of the bonds the next update draws; the field is not changed. */
+int sw_phi4_labels(sw_phi4* h, int32_t* out, int32_t out_is_device);
+
+/* Counter of the next update. */
+int sw_phi4_get_sweep(sw_phi4* h, uint32_t* t_out);
+
+/* Release the field (synchronises its stream). NULL is a no-op. */
+int sw_phi4_destroy(sw_phi4* h);
+
 /* Largest side accepted by sw_sweep_noalloc. */
 #define SW_NOALLOC_MAX_L 1024
 

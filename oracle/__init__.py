@@ -39,6 +39,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sw_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "phi4_oracle.c")]
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -51,10 +52,11 @@ def build(force: bool = False) -> str:
     """Compile sw_oracle.c into _build/liboracle.so (plain C, -O2)."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    # ISO C mode: no floating-point contraction beyond the explicit fma calls
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -104,6 +106,23 @@ def _load():
         lib.oracle_potts_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
                                          ctypes.c_uint32, ctypes.c_int, P, P, P]
         lib.oracle_potts_run.restype = ctypes.c_int
+        D = ctypes.c_double
+        lib.phi4_exp_neg.argtypes = [D]
+        lib.phi4_exp_neg.restype = D
+        lib.phi4_direction.argtypes = [ctypes.c_uint64, ctypes.c_uint32, P]
+        lib.phi4_direction.restype = ctypes.c_int
+        lib.phi4_init.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, P]
+        lib.phi4_init.restype = None
+        lib.phi4_bonds.argtypes = [ctypes.c_int, D, ctypes.c_uint64, ctypes.c_uint32, P, P, P]
+        lib.phi4_bonds.restype = None
+        lib.phi4_labels.argtypes = [ctypes.c_int, P, P, P]
+        lib.phi4_labels.restype = ctypes.c_int64
+        lib.phi4_reflect.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, P, P, P]
+        lib.phi4_reflect.restype = None
+        lib.phi4_observe.argtypes = [ctypes.c_int, P, P, P]
+        lib.phi4_observe.restype = None
+        lib.phi4_run.argtypes = [ctypes.c_int, D, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, P, P, P]
+        lib.phi4_run.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -304,3 +323,71 @@ def potts_run(L: int, q: int, beta: float, seed: int, n: int, *, states: np.ndar
     if _load().oracle_potts_run(L, q, float(beta), seed, t0 & 0xffffffff, n, _ptr(s), _ptr(E), _ptr(M)) != 0:
         raise MemoryError("oracle_potts_run: allocation failed")
     return s, E[:n], M[:n]
+
+
+# ------------------------------------------------- O(4) phi^4 multicluster
+# §3's update (Eqs. 2 and 3) on an L^4 torus; see phi4_oracle.c (O1-O5).
+
+def phi4_exp_neg(z: float) -> float:
+    return float(_load().phi4_exp_neg(float(z)))
+
+
+def phi4_direction(seed: int, t: int) -> np.ndarray:
+    r = np.zeros(4)
+    if _load().phi4_direction(seed, t & 0xffffffff, _ptr(r)) != 0:
+        raise RuntimeError("phi4_direction: no direction found")
+    return r
+
+
+def phi4_init(L: int, seed: int, cold: bool = False) -> np.ndarray:
+    phi = np.zeros((L, L, L, L, 4))
+    _load().phi4_init(L, seed, 1 if cold else 0, _ptr(phi))
+    return phi
+
+
+def phi4_bonds(phi: np.ndarray, kappa: float, seed: int, t: int, r: np.ndarray) -> np.ndarray:
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    L = phi.shape[0]
+    b = np.zeros((L, L, L, L), np.uint8)
+    _load().phi4_bonds(L, float(kappa), seed, t & 0xffffffff, _ptr(phi), _ptr(np.ascontiguousarray(r, np.float64)),
+                       _ptr(b))
+    return b
+
+
+def phi4_labels(bonds: np.ndarray):
+    b = np.ascontiguousarray(bonds, dtype=np.uint8)
+    L = b.shape[0]
+    lab = np.zeros(b.shape, np.int32)
+    queue = np.zeros(b.size, np.int32)
+    n = _load().phi4_labels(L, _ptr(b), _ptr(lab), _ptr(queue))
+    return lab, int(n)
+
+
+def phi4_reflect(phi: np.ndarray, lab: np.ndarray, seed: int, t: int, r: np.ndarray) -> np.ndarray:
+    out = np.array(phi, dtype=np.float64, copy=True, order="C")
+    L = out.shape[0]
+    _load().phi4_reflect(L, seed, t & 0xffffffff, _ptr(np.ascontiguousarray(lab, np.int32)),
+                         _ptr(np.ascontiguousarray(r, np.float64)), _ptr(out))
+    return out
+
+
+def phi4_observe(phi: np.ndarray):
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    E = np.zeros(1)
+    M = np.zeros(4)
+    _load().phi4_observe(phi.shape[0], _ptr(phi), _ptr(E), _ptr(M))
+    return float(E[0]), M
+
+
+def phi4_run(L: int, kappa: float, seed: int, n: int, *, phi: np.ndarray | None = None, cold: bool = False,
+             t0: int = 0):
+    """n multicluster updates; returns (field [L,L,L,L,4], E [n], M [n,4])."""
+    if not (2 <= L and L**4 < 2**31):
+        raise ValueError("L outside 2 <= L, L^4 < 2^31")
+    f = phi4_init(L, seed, cold) if phi is None else np.array(phi, dtype=np.float64, copy=True, order="C")
+    E = np.zeros(max(n, 1))
+    M = np.zeros((max(n, 1), 4))
+    rc = _load().phi4_run(L, float(kappa), seed, t0 & 0xffffffff, n, _ptr(f), _ptr(E), _ptr(M))
+    if rc != 0:
+        raise RuntimeError(f"phi4_run failed ({rc})")
+    return f, E[:n], M[:n]

@@ -84,6 +84,16 @@ SIGNATURES = {
     "sw_potts_labels": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "sw_potts_get_sweep": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32)]),
     "sw_potts_destroy": (ctypes.c_int, [_P]),
+    "sw_phi4_direction": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, _P]),
+    "sw_phi4_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32, _P,
+                                      ctypes.POINTER(_P)]),
+    "sw_phi4_sweep": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sw_phi4_observables": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "sw_phi4_field": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "sw_phi4_set_field": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_int32]),
+    "sw_phi4_labels": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "sw_phi4_get_sweep": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32)]),
+    "sw_phi4_destroy": (ctypes.c_int, [_P]),
 }
 SW_NOALLOC_MAX_L = 1024
 
@@ -446,6 +456,75 @@ class Potts:
     def close(self) -> None:
         if self.h:
             _lib.sw_potts_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# --------------------------------------------------- O(4) phi^4 multicluster
+
+def sw_phi4_direction(seed: int, t: int) -> np.ndarray:
+    r = np.zeros(4)
+    _check(_lib.sw_phi4_direction(int(seed) & 0xFFFFFFFFFFFFFFFF, int(t) & 0xFFFFFFFF, _host_ptr(r)),
+           "sw_phi4_direction")
+    return r
+
+
+class Phi4:
+    """Owning wrapper of one sw_phi4 handle (field double [L, L, L, L, 4])."""
+
+    def __init__(self, L: int, kappa: float, seed: int, init: int = SW_INIT_HOT, stream: int | None = None):
+        self.L = int(L)
+        h = ctypes.c_void_p()
+        _check(_lib.sw_phi4_create(int(L), float(kappa), int(seed) & 0xFFFFFFFFFFFFFFFF, int(init),
+                                   ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)), "sw_phi4_create")
+        self.h = h.value
+
+    def sweep(self, n: int = 1) -> None:
+        _check(_lib.sw_phi4_sweep(self.h, int(n)), "sw_phi4_sweep")
+
+    @property
+    def t(self) -> int:
+        t = ctypes.c_uint32()
+        _check(_lib.sw_phi4_get_sweep(self.h, ctypes.byref(t)), "sw_phi4_get_sweep")
+        return t.value
+
+    def observables(self, first: int, count: int):
+        E = np.zeros(max(count, 0))
+        M = np.zeros((max(count, 0), 4))
+        _check(_lib.sw_phi4_observables(self.h, int(first), int(count), _host_ptr(E), _host_ptr(M)),
+               "sw_phi4_observables")
+        return E, M
+
+    def field(self) -> np.ndarray:
+        L = self.L
+        out = np.zeros((L, L, L, L, 4))
+        _check(_lib.sw_phi4_field(self.h, _host_ptr(out), 0), "sw_phi4_field")
+        return out
+
+    def set_field(self, phi, t: int) -> None:
+        a = np.ascontiguousarray(phi, dtype=np.float64)
+        assert a.shape == (self.L,) * 4 + (4,)
+        _check(_lib.sw_phi4_set_field(self.h, _host_ptr(a), int(t) & 0xFFFFFFFF, 0), "sw_phi4_set_field")
+
+    def labels(self) -> np.ndarray:
+        out = np.zeros((self.L,) * 4, np.int32)
+        _check(_lib.sw_phi4_labels(self.h, _host_ptr(out), 0), "sw_phi4_labels")
+        return out
+
+    def close(self) -> None:
+        if self.h:
+            _lib.sw_phi4_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -17,9 +17,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libsw.so")
-SOURCES = ["sw_kernels.cu", "sw_api.cu", "sw_noalloc.cu", "sw_batch.cu", "sw_small.cu", "sw_equiv.cu", "sw_potts.cu"]
+SOURCES = ["sw_kernels.cu", "sw_api.cu", "sw_noalloc.cu", "sw_batch.cu", "sw_small.cu", "sw_equiv.cu", "sw_potts.cu", "sw_phi4.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC]
 
 

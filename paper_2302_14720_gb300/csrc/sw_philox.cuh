@@ -38,7 +38,7 @@ __host__ __device__ inline KeySchedule make_key_schedule(uint64_t seed) {
   return ks;
 }
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const KeySchedule& ks) {
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const KeySchedule& ks) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint64_t pa = (uint64_t)kPhiloxMulA * c.x;
