@@ -44,9 +44,9 @@ __host__ __device__ constexpr TileShape shape_of(int v) {
          : v == 4 ? TileShape{4, 128, 4, 0}
          : v == 5 ? TileShape{8, 64, 8, 0}
          : v == 6 ? TileShape{4, 64, 2, 0}
-         : v == 7 ? TileShape{4, 64, 2, 1}
-         : v == 8 ? TileShape{4, 64, 2, 2}
-                  : TileShape{4, 64, 2, 3};
+         : v == 7 ? TileShape{4, 32, 2, 0}
+         : v == 8 ? TileShape{8, 32, 2, 0}
+                  : TileShape{16, 32, 2, 0};
 }
 
 // Per-lattice device buffers of the tile pipeline.

@@ -133,3 +133,16 @@ def test_sweep_limit_stops_each_replica_at_its_target(sw):
         assert np.array_equal(sw.sw_batch_observables(b, 0, 0, 7)[0], want_E)
     finally:
         sw.sw_batch_destroy(b)
+
+
+def test_autotune_installs_a_measured_shape(sw):
+    from paper_2302_14720_gb300 import autotune
+    table = autotune.tune([300], shapes=[2, 6])
+    b = autotune.bucket_of(300)
+    assert table[b]["shape"] in (2, 6) and all(v > 0 for v in table[b]["ms"].values())
+    # results do not depend on the shape chosen
+    with sw.Lattice(300, 0.44, 5) as lat:
+        lat.sweep(3)
+        want_s, want_E, _, _ = oracle.run(300, 0.44, 5, 3)
+        assert np.array_equal(lat.spins(), want_s)
+    sw.sw_tune_shape(b, -1)

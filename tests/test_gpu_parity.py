@@ -22,7 +22,7 @@ from workloads import random_spins, striped_spins
 pytestmark = pytest.mark.gpu
 
 BETA_C = 0.44068679
-SHAPES = [0, 2, 6, 9]  # 4-row strips, 64-wide tiles, the default 2-row strips, 3 atomic-free merge rounds
+SHAPES = [0, 2, 6, 8]  # 4-row strips, 64-wide tiles, the default 128x64, 256x32 tiles
 SMALL_L = [2, 3, 5, 17, 31, 32, 33, 64, 65, 100, 127, 128, 129, 191, 257]
 
 
