@@ -647,19 +647,33 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
   __syncthreads();
 
   // the joins leave chains of strip roots (a strip's root hung under the
-  // root of the strip above, and so on); walking them first from the strip
-  // roots, halving as we go, keeps every later walk short
+  // root of the strip above, and so on). Pointer jumping over the strip
+  // roots, each round replacing every parent by its parent's parent, points
+  // all of them at their tile roots in a logarithmic number of rounds; only
+  // a strip root's owner writes it, and every value written is an ancestor.
+  // A strip root whose parent is a root is done for good (the joins are
+  // over), so each round only visits the ones still pending.
+  for (int round = 0; round < 64; ++round) {
+    bool changed = false;
 #pragma unroll
-  for (int r = 0; r < H; ++r) {
-    const int base = (y0r + r) * TW + 32 * w;
-    uint32_t R = sroot[r];
-    while (R) {
-      const int b = __ffs(R) - 1;
-      R &= R - 1;
-      find_shared(par, base + b);
+    for (int r = 0; r < H; ++r) {
+      const int base = (y0r + r) * TW + 32 * w;
+      uint32_t R = sroot[r];
+      while (R) {
+        const int b = __ffs(R) - 1;
+        R &= R - 1;
+        const int x = base + b;
+        const int p = par[x], pp = par[p];
+        if (pp != p) {
+          par[x] = (uint16_t)pp;
+          changed = true;
+        } else {
+          sroot[r] &= ~(1u << b);
+        }
+      }
     }
+    if (!__syncthreads_or(changed)) break;
   }
-  __syncthreads();
 
   // every run start of my strip points at its tile root. Most run starts
   // are at most two hops from it, so they are taken four at a time with
