@@ -1194,11 +1194,21 @@ __global__ void init_kernel(int8_t* spins, long long n, KeySchedule ks, int cold
   }
 }
 
+// Every spin must be +1 (0x01) or -1 (0xFF). 16 bytes per thread step,
+// four at a time with byte-wise compares; the buffer is the library's own
+// (16-byte aligned), the ragged tail goes byte by byte.
 __global__ void check_spins_kernel(const int8_t* spins, long long n, int* err) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int8_t v = spins[i];
-    if (v != 1 && v != -1) atomicCAS(err, 0, kErrBadSpin);
+  const long long stride = (long long)gridDim.x * blockDim.x, i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nv = n / 16;
+  const uint4* p = reinterpret_cast<const uint4*>(spins);
+  auto ok4 = [](uint32_t w) { return (__vcmpeq4(w, 0x01010101u) | __vcmpeq4(w, 0xFFFFFFFFu)) == 0xFFFFFFFFu; };
+  bool bad = false;
+  for (long long i = i0; i < nv; i += stride) {
+    const uint4 v = p[i];
+    bad |= !(ok4(v.x) && ok4(v.y) && ok4(v.z) && ok4(v.w));
   }
+  for (long long i = 16 * nv + i0; i < n; i += stride) bad |= spins[i] != 1 && spins[i] != -1;
+  if (bad) atomicCAS(err, 0, kErrBadSpin);
 }
 
 template <int WPR, int TH, int H>

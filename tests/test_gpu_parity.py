@@ -272,3 +272,22 @@ def test_error_statuses(sw):
         lat.set_state(np.ones((L, L), np.int8), 0)
         lat.sweep(1)
         lat.observables(0, 1)
+
+
+@pytest.mark.parametrize("L", [16, 17, 33, 1000])
+@pytest.mark.parametrize("where", ["first", "middle", "last"])
+@pytest.mark.parametrize("value", [0, 2, -2, 127, -128])
+def test_set_state_rejects_every_invalid_spin(sw, L, where, value):
+    # the check reads 16 bytes at a time with a byte-wise tail: a bad value
+    # in the first byte, inside a vector, and in the last byte (the tail
+    # when L*L is not a multiple of 16) must all be caught
+    s = np.ones((L, L), np.int8)
+    s[::3] = -1
+    idx = {"first": 0, "middle": (L * L) // 2 + 5, "last": L * L - 1}[where]
+    s.reshape(-1)[idx] = value
+    with make(sw, L, 0.4, 1) as lat:
+        lat.sweep(1)
+        with pytest.raises(sw.SWError) as ei:
+            lat.set_state(s, 0)
+        assert ei.value.status == sw.SW_EINVAL
+        assert lat.t == 1
