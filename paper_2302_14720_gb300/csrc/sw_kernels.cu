@@ -511,17 +511,27 @@ __device__ __forceinline__ bool cta_args(const SweepArgs& a0, const BatchArgs& b
 
 // ================================================================ phase 1
 
+// Two-row strips keep few values live, so those shapes ask for 1280 resident
+// threads an SM (at most 51 registers a thread; ten CTAs of 128 threads also
+// fit their ~21 KB of shared memory). Taller strips would spill under that
+// bound and keep the compiler's choice.
+template <int NT, int H>
+constexpr int phase1_min_blocks() {
+  return H == 2 ? 1280 / NT : 1;
+}
+
 template <int WPR, int TH, int H, int PL, bool BATCH>
-__global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs a0, const BatchArgs bat) {
+__global__ void __launch_bounds__(WPR * (TH / H), phase1_min_blocks<WPR * (TH / H), H>())
+    phase1_kernel(const SweepArgs a0, const BatchArgs bat) {
   using T = Tile<WPR, TH, H>;
   constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
   __shared__ __align__(16) uint16_t par[TH * TW];
-  __shared__ uint32_t s_spin[TH][WPR];
+  __shared__ uint32_t s_spin[TH][WPR];  // the spin bits while drawing bonds, then the border-root marks
   __shared__ uint32_t s_eint[TH][WPR];
   __shared__ uint32_t s_dint[TH][WPR];
   __shared__ uint32_t s_bb[BBW];
-  __shared__ int s_broot[NB];
-  __shared__ uint32_t s_bmask[RW];   // border roots
+  __shared__ int16_t s_broot[NB];
+  uint32_t* const s_bmask = &s_spin[0][0];  // border roots (RW words), once the bonds are drawn
   __shared__ uint32_t s_pre[RW];     // prefix counts of s_bmask
   __shared__ uint32_t s_wsum[33];
 
@@ -540,7 +550,6 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
   uint32_t* hS = s_bb + T::OFF_HS;
 
   for (int i = tid; i < BBW; i += NT) s_bb[i] = 0u;
-  for (int i = tid; i < RW; i += NT) s_bmask[i] = 0u;
 
   // ---- spins of my strip
   const int nb = max(0, min(32, P.ncols - 32 * w));
@@ -641,6 +650,7 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
     }
   }
   __syncthreads();
+  for (int i = tid; i < RW; i += NT) s_bmask[i] = 0u;  // the spin bits are no longer needed
   // s_pre is free until the border slots: it holds the warps' join queues
   static_assert((NT / 32) * 64 <= RW, "join queues fit in s_pre");
   strip_joins<WPR, TH, H, PL>(par, e_int, wmask, y0r, nv, w, k, s_eint, s_dint, s_pre + (tid >> 5) * 64, a.tb.err);
@@ -717,7 +727,7 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase1_kernel(const SweepArgs 
       r = par[y * TW + (x & ~31) + run_start(~(s_eint[y][x >> 5] << 1), x & 31)];
       atomicOr(&s_bmask[r >> 5], 1u << (r & 31));
     }
-    s_broot[j] = r;
+    s_broot[j] = (int16_t)r;
   }
   __syncthreads();
   const int nsl = block_popc_prefix<RW, NT>(s_bmask, s_pre, s_wsum);
