@@ -166,6 +166,22 @@ def test_full_size_spot_sweep(sw, beta, p_minus):
     assert E[0] == want_E[0] and M[0] == want_M[0]
 
 
+def test_maximum_size_sweep(sw):
+    """The largest lattice the ABI accepts (L*L < 2^31): 2.1 G sites, tiles
+    4 columns wide on the right and 4 rows high at the bottom, site keys
+    near 2^31. Both sides take the C7 hot start themselves; one sweep's
+    spins, E and M must agree exactly (the oracle needs about two minutes)."""
+    L, seed = 46340, 11
+    assert L * L < 2**31 <= (L + 1) * (L + 1)
+    with make(sw, L, BETA_C, seed) as lat:
+        lat.sweep(1)
+        E, M = lat.observables(0, 1)
+        spins = lat.spins()
+    want_s, want_E, want_M, _ = oracle.run(L, BETA_C, seed, 1)
+    assert E[0] == want_E[0] and M[0] == want_M[0]
+    assert np.array_equal(spins, want_s)
+
+
 # ---------------------------------------------------------------- invariants
 
 def test_sweep_composition(sw):

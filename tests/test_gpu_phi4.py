@@ -41,6 +41,21 @@ def test_phi4_chain_parity(sw, L, kappa, cold):
         assert np.abs(M - wM).max() <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("L", [16, 28])
+def test_phi4_bench_configuration(sw, L):
+    """The benchmark's runs (kappa = 0.304, hot start, seed 6) at the
+    smallest and largest L of the paper's table, five updates."""
+    seed, n = 6, 5
+    with sw.Phi4(L, KAPPA, seed) as f:
+        f.sweep(n)
+        want, wE, wM = oracle.phi4_run(L, KAPPA, seed, n)
+        assert np.array_equal(f.field(), want)
+        E, M = f.observables(0, n)
+        scale = 4 * L**4 * np.abs(want).max() ** 2 + 1.0
+        assert np.abs(E - wE).max() <= 1e-12 * scale
+        assert np.abs(M - wM).max() <= 1e-12 * scale
+
+
 def test_phi4_labels_and_set_field(sw):
     L, seed, t = 6, 5, 9
     rng = np.random.default_rng(2)

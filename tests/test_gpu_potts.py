@@ -32,6 +32,18 @@ def test_potts_chain_parity(sw, L, q, beta, cold):
         assert np.array_equal(p.states(), want_s)
 
 
+def test_potts_bench_configuration(sw):
+    """The benchmark's Potts run (L = 1024, q = 3 at its critical coupling
+    ln(1 + sqrt 3), hot start, seed 4), ten sweeps, element by element."""
+    L, q, beta, seed, n = 1024, 3, 1.0050833, 4, 10
+    with sw.Potts(L, q, beta, seed) as p:
+        p.sweep(n)
+        E, M = p.observables(0, n)
+        want_s, want_E, want_M = oracle.potts_run(L, q, beta, seed, n)
+        assert np.array_equal(E, want_E) and np.array_equal(M, want_M)
+        assert np.array_equal(p.states(), want_s)
+
+
 def test_potts_q2_equals_ising_assign(sw):
     L, beta, seed, n = 96, 0.43, 21, 6
     with sw.Potts(L, 2, 2 * beta, seed) as p, sw.Lattice(L, beta, seed) as lat:
