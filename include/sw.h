@@ -34,9 +34,11 @@
  *  C5  Bond draws of sweep t: counter (site>>1, t, 0, 0); site i takes word
  *      x[2*(i&1) + dir], dir 0 = east, 1 = south. One Philox block serves two
  *      consecutive sites and both directions.
- *  C6  Cluster flip of sweep t: counter (root, t, 1, 0), word x0, where root
- *      is the cluster's canonical label (C9). The cluster flips iff
- *      x0 >> 31 == 1; then every site of it takes s <- -s. (The paper's
+ *  C6  Cluster flip of sweep t: one output bit per site index. Block
+ *      (b, t, 1, 0) serves the indices 128b .. 128b+127 in order: index i
+ *      takes bit (i & 31) of word x[(i >> 5) & 3] of block (i >> 7, t, 1, 0).
+ *      The cluster whose canonical label (C9) is root flips iff the bit of
+ *      index root is 1; then every site of it takes s <- -s. (The paper's
  *      §2.4 assigns each cluster a fresh random spin; with monochrome
  *      clusters both rules give the same distribution.)
  *  C6b Assignment rule (optional, sw_set_rule / sw_batch_set_rule, §2.4 as

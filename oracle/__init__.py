@@ -182,7 +182,8 @@ def labels(bond_bits: np.ndarray):
 
 
 def flip(spins: np.ndarray, lab: np.ndarray, seed: int, t: int) -> np.ndarray:
-    """New spins (§2.4): cluster rooted at r flips iff Philox (r,t,1,0).x0 >> 31."""
+    """New spins (§2.4): cluster rooted at r flips iff bit r % 32 of word
+    (r // 32) % 4 of Philox block (r // 128, t, 1, 0) is set."""
     s = np.array(spins, dtype=np.int8, copy=True, order="C")
     lab = np.ascontiguousarray(lab, dtype=np.int32)
     _load().oracle_flip(s.shape[0], seed, t & 0xffffffff, _ptr(lab), _ptr(s))

@@ -18,8 +18,8 @@
  *   3. clusters (§2.3): breadth-first search over the bond graph, sources
  *      taken in increasing site order, so every site receives the smallest
  *      site index of its cluster (the "lowest value label");
- *   4. new spins (§2.4): cluster with root r flips iff the top bit of the
- *      Philox word drawn for (r, t) is set;
+ *   4. new spins (§2.4): cluster with root r flips iff the Philox bit drawn
+ *      for index r in sweep t is set (one block per 128 indices);
  *   5. bonds are dropped (§2.5);
  *   then E = -sum over the 2N edges of s_i s_j and M = sum s_i (end of §2).
  *
@@ -161,14 +161,17 @@ int64_t oracle_labels(int L, const uint8_t* bonds, int32_t* label, int32_t* queu
 
 /* ------------------------------------------------------------------- flip */
 
-/* §2.4 with the flip reading: the cluster rooted at r flips iff the top bit
- * of word x0 of Philox block (r, t, 1, 0) is set. */
+/* §2.4 with the flip reading: Philox block (b, t, 1, 0) holds one bit for
+ * each of the site indices 128b .. 128b+127, words x0..x3 in order, bit 0
+ * first; the cluster rooted at r flips iff the bit of index r is set. */
 void oracle_flip(int L, uint64_t seed, uint32_t t, const int32_t* label, int8_t* s) {
     int64_t N = (int64_t)L * L;
     for (int64_t i = 0; i < N; ++i) {
+        uint32_t r = (uint32_t)label[i];
         uint32_t w[4];
-        philox_seeded(seed, (uint32_t)label[i], t, 1u, 0u, w);
-        if (w[0] >> 31) s[i] = (int8_t)(-s[i]);
+        philox_seeded(seed, r / 128u, t, 1u, 0u, w);
+        uint32_t bit = (w[(r % 128u) / 32u] >> (r % 32u)) & 1u;
+        if (bit) s[i] = (int8_t)(-s[i]);
     }
 }
 

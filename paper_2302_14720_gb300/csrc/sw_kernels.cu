@@ -686,8 +686,8 @@ __global__ void __launch_bounds__(WPR * (TH / H), phase1_min_blocks<WPR * (TH / 
   }
 
   // every run start of my strip points at its tile root. Most run starts
-  // are at most two hops from it, so they are taken four at a time with
-  // their two hops loaded side by side; longer paths finish one by one.
+  // are at most two hops from it (parent and grandparent read back to
+  // back); longer paths finish through find_final.
   uint32_t rootbits[H];  // run starts that are tile roots
 #pragma unroll
   for (int r = 0; r < H; ++r) {
@@ -696,26 +696,11 @@ __global__ void __launch_bounds__(WPR * (TH / H), phase1_min_blocks<WPR * (TH / 
     const int base = (y0r + r) * TW + 32 * w;
     uint32_t R = ~(e_int[r] << 1) & wmask;
     while (R) {
-      constexpr int G = 4;
-      int x[G], p[G], pp[G];
-#pragma unroll
-      for (int q = 0; q < G; ++q) {
-        x[q] = -1;
-        if (R) {
-          x[q] = base + __ffs(R) - 1;
-          R &= R - 1;
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < G; ++q) p[q] = x[q] >= 0 ? par[x[q]] : 0;
-#pragma unroll
-      for (int q = 0; q < G; ++q) pp[q] = x[q] >= 0 ? par[p[q]] : 0;
-#pragma unroll
-      for (int q = 0; q < G; ++q) {
-        if (x[q] < 0) continue;
-        if (p[q] == x[q]) rootbits[r] |= 1u << (x[q] - base);
-        par[x[q]] = (uint16_t)(pp[q] == p[q] ? p[q] : find_final(par, pp[q]));
-      }
+      const int b = __ffs(R) - 1;
+      R &= R - 1;
+      const int x = base + b, p = par[x], pp = par[p];
+      if (p == x) rootbits[r] |= 1u << b;
+      par[x] = (uint16_t)(pp == p ? p : find_final(par, pp));
     }
   }
   __syncthreads();
@@ -937,10 +922,12 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
   __syncthreads();
 
   // ---- decision bit of every root of my strip: border roots from their slot,
-  // the others from one Philox block each (C6, or the assignment rule).
-  // Phase 1 marked the roots. The lanes of a warp walk their inner roots in
-  // step and queue them (in s_snew, free until the new spins); the queue is
-  // drawn 64 roots at a time, two independent draws per lane.
+  // the others drawn here (phase 1 marked the roots). Under the flip rule
+  // (C6) one Philox block holds the bits of 128 consecutive site indices, so
+  // a row word's inner roots take their bits from one draw. Under the
+  // assignment rule each root draws its own block: the lanes of a warp walk
+  // their inner roots in step and queue them (in s_snew, free until the new
+  // spins); the queue is drawn 64 roots at a time, two draws per lane.
   if (!LABELS) {
     const int warp = tid >> 5;
     constexpr int QC = 128;  // queue entries per warp
@@ -966,6 +953,10 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
         B &= B - 1;
         const int sl = slot_of(s_bmask, s_pre, base + b);
         fl |= (sl < nsl ? (uint32_t)s_slotval[sl] : 0u) << b;
+      }
+      if (!a.rule && inner) {
+        fl |= flip_bits32((uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w), a.t, a.ks) & inner;
+        inner = 0u;
       }
       if (fl) atomicOr(&s_flip[rw], fl);
       while (__any_sync(0xffffffffu, inner != 0u)) {

@@ -49,10 +49,28 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const KeySchedu
   return c;
 }
 
-// C6: the cluster rooted at site `root` flips in sweep t iff the top bit of
-// word x0 of block (root, t, 1, 0) is set.
+__device__ __forceinline__ uint32_t word_of(const uint4& q, uint32_t j) {
+  return j == 0u ? q.x : j == 1u ? q.y : j == 2u ? q.z : q.w;
+}
+
+// C6: site index i owns bit (i & 31) of word (i >> 5) & 3 of block
+// (i >> 7, t, 1, 0); the cluster rooted at `root` flips in sweep t iff the
+// bit of index root is set.
 __device__ __forceinline__ uint32_t flip_bit(uint32_t root, uint32_t t, const KeySchedule& ks) {
-  return philox4x32_10(make_uint4(root, t, 1u, 0u), ks).x >> 31;
+  const uint4 q = philox4x32_10(make_uint4(root >> 7, t, 1u, 0u), ks);
+  return (word_of(q, (root >> 5) & 3u) >> (root & 31u)) & 1u;
+}
+
+// The C6 bits of the 32 consecutive indices i0 .. i0+31 (bit k for i0 + k):
+// one block when i0 is a multiple of 32, else the two 32-bit words that the
+// range straddles (a second block only when they lie in different blocks).
+__device__ __forceinline__ uint32_t flip_bits32(uint32_t i0, uint32_t t, const KeySchedule& ks) {
+  const uint32_t a = i0 >> 5, o = i0 & 31u, j = a & 3u;
+  const uint4 q = philox4x32_10(make_uint4(a >> 2, t, 1u, 0u), ks);
+  const uint32_t lo = word_of(q, j);
+  if (o == 0u) return lo;
+  const uint32_t hi = j < 3u ? word_of(q, j + 1u) : philox4x32_10(make_uint4((a >> 2) + 1u, t, 1u, 0u), ks).x;
+  return (lo >> o) | (hi << (32u - o));
 }
 
 // §2.4 as printed (the assignment rule): the cluster rooted at `root` gets

@@ -306,13 +306,16 @@ def test_bond_words_and_strict_threshold(L):
                 assert (above >> d) & 1 == 1
 
 
-def test_flip_word_and_bit():
-    # beta = 0: no bonds, every site is its own root, so site i flips iff the
-    # top bit of word x0 of block (i, t, 1, 0) is set.
-    L, seed, t = 7, 99, 5
+@pytest.mark.parametrize("L", [7, 16, 23])
+def test_flip_word_and_bit(L):
+    # beta = 0: no bonds, every site is its own root, so the flips of sites
+    # 0 .. N-1 are the bit stream of blocks (0, t, 1, 0), (1, t, 1, 0), ...:
+    # words x0..x3 of each block in order, bit 0 of a word first.
+    seed, t = 99, 5
     s = random_spins(L, seed=3)
     out, _, _, _ = oracle.run(L, 0.0, seed, 1, spins=s, t0=t)
-    for i in range(L * L):
-        x0 = oracle.philox((i, t, 1, 0), _key(seed))[0]
-        want = -s.reshape(-1)[i] if x0 >> 31 else s.reshape(-1)[i]
-        assert out.reshape(-1)[i] == want
+    N = L * L
+    words = np.concatenate([oracle.philox((b, t, 1, 0), _key(seed)) for b in range((N + 127) // 128)])
+    stream = np.unpackbits(words.astype("<u4").view(np.uint8), bitorder="little")[:N]
+    want = np.where(stream == 1, -s.reshape(-1), s.reshape(-1))
+    assert np.array_equal(out.reshape(-1), want)
