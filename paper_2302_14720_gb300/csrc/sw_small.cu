@@ -9,8 +9,10 @@
 //   clusters (§2.3)   the two ends of every bond are united, the larger root
 //                     hung under the smaller, so every root is its
 //                     cluster's smallest site (C9);
-//   new spins (§2.4)  each root draws its decision (C6, or C6b's fresh
-//                     spin); a warp per row word sets its 32 sites;
+//   new spins (§2.4)  the flip bits of all site indices are filled from
+//                     their blocks and each root reads its own (C6), or
+//                     each root draws C6b's fresh spin; a warp per row
+//                     word sets its 32 sites;
 //   E and M (C10)     from the new bit masks, int64, one trace row per sweep.
 // Spins are read at the start and written back after the last sweep.
 #include <cuda_runtime.h>
@@ -80,7 +82,7 @@ __device__ __forceinline__ T small_warp_sum(T v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kSmallThreads) small_sweep_kernel(const SmallArgs a) {
+__global__ void __launch_bounds__(kSmallThreads, 1) small_sweep_kernel(const SmallArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   constexpr int NT = kSmallThreads, NW = NT / 32;
   __shared__ long long s_red[2][NW];
@@ -139,8 +141,21 @@ __global__ void __launch_bounds__(kSmallThreads) small_sweep_kernel(const SmallA
     }
     __syncthreads();
 
-    // ---- every site points at its root; roots draw their decision (C6 /
-    // C6b), queued per warp and drawn 32 at a time so that every lane draws
+    // ---- every site points at its root; roots draw their decision. Flip
+    // rule (C6): word k of s_dec, the bits of site indices 32k .. 32k+31, is
+    // word k & 3 of block k >> 2, so every word is filled from its block and
+    // each root reads its own bit. Assignment rule (C6b): the roots are
+    // queued per warp and drawn 32 at a time so that every lane draws.
+    const bool flip_rule = a.rule == 0;
+    if (flip_rule) {
+      for (int b = tid; 4 * b < DW; b += NT) {
+        const uint4 q4 = philox4x32_10(make_uint4((uint32_t)b, t, 1u, 0u), a.ks);
+        s_dec[4 * b] = q4.x;
+        if (4 * b + 1 < DW) s_dec[4 * b + 1] = q4.y;
+        if (4 * b + 2 < DW) s_dec[4 * b + 2] = q4.z;
+        if (4 * b + 3 < DW) s_dec[4 * b + 3] = q4.w;
+      }
+    }
     {
       uint16_t* q = s_rootq[warp];
       int qh = 0, qn = 0;  // the same in every lane of the warp
@@ -154,7 +169,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_sweep_kernel(const SmallA
             p = par[r];
           }
           par[i] = (uint16_t)r;  // concurrent stores all write roots
-          isroot = r == i;
+          isroot = r == i && !flip_rule;
         }
         const uint32_t m = __ballot_sync(0xffffffffu, isroot);
         if (isroot) q[(qh + qn + __popc(m & ((1u << lane) - 1u))) & 63] = (uint16_t)i;
