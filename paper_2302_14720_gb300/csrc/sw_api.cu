@@ -231,6 +231,7 @@ int sync_and_check(sw_lattice* h) {
     case sw::kErrUnionCap: return fail(SW_ETIMEOUT, "device union-find retry loop reached its cap");
     case sw::kErrBadSpin: return fail(SW_EINVAL, "sw_set_state: device spins contain values other than +1/-1");
     case sw::kErrSlotOverflow: return fail(SW_EDEVICE, "device: tile border slots overflowed");
+    case sw::kErrCopyTimeout: return fail(SW_ETIMEOUT, "device: a bulk copy into shared memory did not complete");
     default: return fail(SW_EDEVICE, "device error flag %d", flag);
   }
 }

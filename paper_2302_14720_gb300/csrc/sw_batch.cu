@@ -223,6 +223,7 @@ int sync_and_check_batch(sw_batch* b) {
   int flag = 0;
   B_CUDA(cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag read");
   if (flag == sw::kErrUnionCap) return bfail(SW_ETIMEOUT, "device union-find retry loop reached its cap");
+  if (flag == sw::kErrCopyTimeout) return bfail(SW_ETIMEOUT, "device bulk copy into shared memory did not complete");
   if (flag != 0) return bfail(SW_EDEVICE, "device error flag set");
   return SW_OK;
 }

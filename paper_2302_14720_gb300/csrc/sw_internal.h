@@ -14,6 +14,7 @@ enum DeviceError : int {
   kErrUnionCap = 1,     // a union-find retry loop hit its iteration cap
   kErrBadSpin = 2,      // sw_set_state from device memory saw a value other than +1/-1
   kErrSlotOverflow = 3, // more boundary components than slots (cannot happen; checked)
+  kErrCopyTimeout = 4,  // a bulk copy into shared memory did not land within its time limit
 };
 
 // A tile shape: TW = 32*WPR columns by TH rows. Each thread owns one 32-site

@@ -57,6 +57,7 @@ constexpr int kUnionCap = 1 << 20;        // retries of one shared-memory union
 constexpr int kGlobalUnionCap = 1 << 16;  // retries of one global union
 constexpr int kGlobalFindCap = 1 << 20;   // steps of one global find
 constexpr int kFlagClaim = 0x40000000;
+constexpr long long kBulkWaitCycles = 1LL << 31;  // ~1 s at the SM clock: limit of a bulk-copy wait
 
 // Highest run start at or below bit b (R always has bit 0 set for valid b).
 __device__ __forceinline__ int run_start(uint32_t R, int b) {
@@ -436,6 +437,41 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 __device__ __forceinline__ int log2_floor(uint32_t v) { return 31 - __clz(v); }
 
+// --------------------------------------------- bulk copies into shared memory
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Called by one thread: start a copy of `bytes` from global memory at src to
+// shared memory at dst on the copy engine (cp.async.bulk; both addresses
+// 16-byte aligned, bytes a multiple of 16), its completion counted on the
+// mbarrier `bar` (initialised here for one arrival plus the transaction
+// bytes). Other threads may wait on `bar` only after a block barrier.
+__device__ __forceinline__ void bulk_load_start(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Wait until the copy counted on `bar` has landed; false after about a
+// second without completion.
+__device__ __forceinline__ bool bulk_load_wait(unsigned long long* bar) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar))
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kBulkWaitCycles) return false;
+  }
+}
+
 // Exclusive prefix sums of popc(mask[i]), i < RW, into pre[i]; returns the
 // total. Words are split into contiguous chunks of C per thread. Called by
 // every thread of the block (contains barriers).
@@ -511,17 +547,17 @@ __device__ __forceinline__ bool cta_args(const SweepArgs& a0, const BatchArgs& b
 
 // ================================================================ phase 1
 
-// Two-row strips keep few values live, so those shapes ask for 1280 resident
-// threads an SM (at most 51 registers a thread; ten CTAs of 128 threads also
-// fit their ~21 KB of shared memory). Taller strips would spill under that
-// bound and keep the compiler's choice.
+// Two-row strips keep few values live, so phases 1 and 3 of those shapes ask
+// for 1280 resident threads an SM (at most 51 registers a thread; ten CTAs
+// of 128 threads also fit their ~22 KB of shared memory). Taller strips
+// would spill under that bound and keep the compiler's choice.
 template <int NT, int H>
-constexpr int phase1_min_blocks() {
+constexpr int strip_min_blocks() {
   return H == 2 ? 1280 / NT : 1;
 }
 
 template <int WPR, int TH, int H, int PL, bool BATCH>
-__global__ void __launch_bounds__(WPR * (TH / H), phase1_min_blocks<WPR * (TH / H), H>())
+__global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H), H>())
     phase1_kernel(const SweepArgs a0, const BatchArgs bat) {
   using T = Tile<WPR, TH, H>;
   constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
@@ -856,7 +892,8 @@ __global__ void resolve_kernel(const SweepArgs a0, const BatchArgs bat) {
 
 // MODE 0: flips + E/M; 1: flips + E/M + cluster sizes; 2: canonical labels.
 template <int WPR, int TH, int H, int MODE, bool BATCH>
-__global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs a0, const BatchArgs bat) {
+__global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H), H>())
+    phase3_kernel(const SweepArgs a0, const BatchArgs bat) {
   using T = Tile<WPR, TH, H>;
   constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
   constexpr bool HIST = MODE == 1, LABELS = MODE == 2;
@@ -871,6 +908,7 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
   __shared__ uint32_t s_hEnew[TH / 32], s_hSnew[TW / 32];
   __shared__ long long s_red[2][NT / 32];
   __shared__ unsigned long long s_hist[HIST ? 34 : 1];
+  __shared__ unsigned long long s_roots_bar;       // completion of the roots tile's bulk copy into par
   extern __shared__ __align__(16) int s_size[];  // HIST: [TH * TW]
 
   SweepArgs a;
@@ -890,6 +928,9 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
   const uint32_t* tb = a.tb.tbits + (size_t)P.tile * 3 * RW;
   const uint16_t* groots = a.tb.roots + (size_t)P.tile * (TW * TH);
   const uint32_t* gbm = a.tb.bmask + (size_t)P.tile * RW;
+  // the tile roots (every tile's block is 16-byte aligned) travel on the
+  // copy engine while the decisions are drawn; the first parent read waits
+  if (tid == 0) bulk_load_start(par, groots, TW * TH * sizeof(uint16_t), &s_roots_bar);
   uint32_t s[H], e_int[H];
 #pragma unroll
   for (int r = 0; r < H; ++r) {
@@ -897,10 +938,6 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
     s[r] = tb[rw];
     e_int[r] = tb[RW + rw] & ~lbit;
     s_bmask[rw] = gbm[rw];
-    const uint4* src = reinterpret_cast<const uint4*>(groots + base);
-    uint4* dst = reinterpret_cast<uint4*>(par + base);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = src[q];
     if (HIST) {
       int4* z = reinterpret_cast<int4*>(s_size + base);
 #pragma unroll
@@ -986,6 +1023,15 @@ __global__ void __launch_bounds__(WPR * (TH / H)) phase3_kernel(const SweepArgs 
       if (draw(x)) atomicOr(&s_flip[x >> 5], 1u << (x & 31));
     }
     __syncthreads();
+  }
+
+  {
+    const bool landed = bulk_load_wait(&s_roots_bar);
+    if (!landed) atomicCAS(a.tb.err, 0, kErrCopyTimeout);
+    if (__syncthreads_or(!landed)) {
+      if (!landed) bulk_load_wait(&s_roots_bar);  // once more before the CTA's shared memory is released
+      return;
+    }
   }
 
   // ---- per run: its root's decision; new spins of my strip
