@@ -222,10 +222,35 @@ __device__ uint64_t find_global(uint64_t* nodes, uint32_t x, int* err) {
   return v;
 }
 
+// Root entries of nodes a and b: the walks of find_global, advanced in step
+// so that the two chains of dependent loads are in flight together.
+__device__ void find_global2(uint64_t* nodes, uint32_t a, uint32_t b, uint64_t& va, uint64_t& vb, int* err) {
+  va = ld_node(nodes + a);
+  vb = ld_node(nodes + b);
+  for (int it = 0;; ++it) {
+    const bool ra = (uint32_t)va == a, rb = (uint32_t)vb == b;
+    if (ra && rb) return;
+    if (it >= kGlobalFindCap) {
+      atomicCAS(err, 0, kErrUnionCap);
+      return;
+    }
+    const uint32_t pa = (uint32_t)va, pb = (uint32_t)vb;
+    const uint64_t wa = ra ? va : ld_node(nodes + pa);  // the parents' entries
+    const uint64_t wb = rb ? vb : ld_node(nodes + pb);
+    const bool ha = !ra && (uint32_t)wa != pa, hb = !rb && (uint32_t)wb != pb;  // parent not a root: halve
+    if (ha) atomicMin(reinterpret_cast<unsigned long long*>(nodes + a), (unsigned long long)wa);
+    if (hb) atomicMin(reinterpret_cast<unsigned long long*>(nodes + b), (unsigned long long)wb);
+    if (!ra) a = ha ? (uint32_t)wa : pa;
+    if (!rb) b = hb ? (uint32_t)wb : pb;
+    va = ha ? ld_node(nodes + a) : wa;  // the grandparents' entries, or the roots'
+    vb = hb ? ld_node(nodes + b) : wb;
+  }
+}
+
 __device__ void unite_global(uint64_t* nodes, uint32_t a, uint32_t b, int* err) {
   for (int it = 0; it < kGlobalUnionCap; ++it) {
-    uint64_t va = find_global(nodes, a, err);
-    uint64_t vb = find_global(nodes, b, err);
+    uint64_t va, vb;
+    find_global2(nodes, a, b, va, vb, err);
     if (va == vb) return;
     if (va < vb) {
       const uint64_t tmp = va;
