@@ -80,49 +80,73 @@ def log(*a):
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 50 ms from construction to stop(); stop()
+    reports the samples whose timestamps fall inside the marked window (the
+    timed region) and, when the window is shorter than the sampling period,
+    the samples of the whole busy span around it."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.path = tempfile.mktemp(prefix="sw_clocks_", suffix=".csv")
         self.proc = None
+        self.window = None
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
+    def mark(self, t0: float, t1: float) -> None:
+        """The timed region, as time.time() values."""
+        self.window = (t0, t1)
+
+    @staticmethod
+    def _epoch(stamp: str):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(stamp, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                sm, smax = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for name, val in zip(names, f[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(name)
+            active = {n for n, v in zip(names, f[6:10]) if v.lower().startswith("active")}
+            rows.append((self._epoch(f[0]), sm, smax, active))
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        inside = rows
+        if self.window is not None:
+            t0, t1 = self.window
+            inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+        use = inside if inside else rows
+        return {"sm_mhz": statistics.median(r[1] for r in use) if use else None,
+                "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "samples": len(use), "samples_in_timed_region": len(inside),
+                "sampled": "timed region" if inside else "warm-up through timed region (region shorter than the 50 ms period)",
+                "reasons": sorted(set().union(*(r[3] for r in use))) if use else []}
 
 
 # ---------------------------------------------------------------- helpers
@@ -233,6 +257,7 @@ def run_ours(args):
     lat = sw.Lattice(L, BETA, seed, sw.SW_INIT_HOT, stream=stream.cuda_stream)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
+    clocks = ClockSampler(local) if rank == 0 else None
     # warm-up (each step preceded by an L2 flush, as in the timed loop)
     for k in range(args.warmup):
         flush.fill_(k & 0xFF)
@@ -242,17 +267,20 @@ def run_ours(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     t_first = lat.t
-    clocks = ClockSampler(local) if rank == 0 else None
     sw.sw_timing(lat.h, True)
     barrier(world)
     torch.cuda.synchronize()
+    t_region0 = time.time()
     for k in range(args.steps):
         flush.fill_((k + 7) & 0xFF)
         starts[k].record(stream)
         lat.sweep(1)
         ends[k].record(stream)
     torch.cuda.synchronize()
+    t_region1 = time.time()
     barrier(world)
+    if clocks:
+        clocks.mark(t_region0, t_region1)
     clock_info = clocks.stop() if clocks else None
     phase_ms, phase_n = sw.sw_timing_read(lat.h)
     sw.sw_timing(lat.h, False)
@@ -268,15 +296,27 @@ def run_ours(args):
     dom_avg_ms = phase_ms[dom] / max(phase_n[dom], 1)
     dom_bytes = PHASE_BYTES_PER_TILE.get(dom, 0) * ntiles
     achieved = dom_bytes / (dom_avg_ms / 1e3) / 1e9
-    traffic = None
+    traffic = warp_instr = None
     tpath = os.path.join(ROOT, "profiles", "dram_traffic_L8192.json")
     if os.path.exists(tpath):
         tr = json.load(open(tpath))
         if tr.get("kernel") == PHASE_NAMES[dom] and tr.get("source_hash") == sw_source_hash():
             traffic = tr.get("bytes_per_launch")
+            warp_instr = tr.get("warp_instructions_per_launch")
     roofline = {"bound": "hbm", "kernel": PHASE_NAMES[dom], "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                 "peak_kind": peak_kind, "bytes_per_launch": dom_bytes, "avg_launch_ms": dom_avg_ms}
+    # What binds the dominant kernel: instruction issue. Its warp instructions
+    # per launch (ncu, same sources) over its live launch time, against one
+    # warp instruction per cycle on each of an SM's 4 schedulers.
+    if warp_instr:
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = (clock_info or {}).get("sm_mhz") or (clock_info or {}).get("sm_max_mhz") or 2070.0
+        issue_peak = n_sm * 4 * mhz * 1e6
+        issue_rate = warp_instr / (dom_avg_ms / 1e3)
+        roofline["issue"] = {"warp_instructions_per_launch": warp_instr, "achieved": issue_rate,
+                             "peak": issue_peak, "unit": "warp instructions/s", "frac": issue_rate / issue_peak,
+                             "peak_from": f"{n_sm} SMs x 4 schedulers x {mhz:.0f} MHz"}
     phases = {PHASE_NAMES[p]: {"ms_per_launch": phase_ms[p] / max(phase_n[p], 1), "launches": int(phase_n[p])}
               for p in range(4) if phase_n[p]}
     sweep_roofline_su_s = hbm_peak * 1e9 / SWEEP_MODEL_BYTES_PER_SITE

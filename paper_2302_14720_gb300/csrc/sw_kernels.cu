@@ -332,10 +332,13 @@ __device__ __forceinline__ uint32_t last_column_bit(int ncols, int w) {
 
 // The tile-local clusters of one thread's strip: parents of its sites set
 // to themselves, then the rows scanned top to bottom. e_int/d_int hold the
-// strip's east and south bonds that stay inside the tile.
+// strip's east and south bonds that stay inside the tile. For two-row
+// strips sroot receives the run starts that are still roots (every link
+// clears the bit of the entry it gives a parent); taller strips leave it to
+// the caller.
 template <int WPR, int H>
 __device__ __forceinline__ void strip_scan(uint16_t* par, const uint32_t (&e_int)[H], const uint32_t (&d_int)[H],
-                                           uint32_t vmask, int y0r, int nv, int w) {
+                                           uint32_t vmask, int y0r, int nv, int w, uint32_t (&sroot)[H]) {
   constexpr int TW = 32 * WPR;
 #pragma unroll
   for (int r = 0; r < H; ++r) {
@@ -356,6 +359,17 @@ __device__ __forceinline__ void strip_scan(uint16_t* par, const uint32_t (&e_int
     // a south bond at j is redundant when j-1 has one and j-1,j share a run in both rows
     uint32_t need = du & ~((du & ep & ec) << 1);
     const int bp = (y0r + r - 1) * TW + 32 * w, bc = bp + TW;
+    if (H == 2) {
+      sroot[0] = Rp;
+      sroot[H - 1] = Rc;
+    }
+    // the entry v (a root of row r-1 or r) gets a parent
+    auto unroot = [&](int v) {
+      if (H == 2) {
+        if (v >= bc) sroot[H - 1] &= ~(1u << (v - bc));
+        else sroot[0] &= ~(1u << (v - bp));
+      }
+    };
     while (need) {
       const int j = __ffs(need) - 1;
       need &= need - 1;
@@ -364,10 +378,16 @@ __device__ __forceinline__ void strip_scan(uint16_t* par, const uint32_t (&e_int
       const int pb = par[B];
       if (pb == B) {
         par[B] = (uint16_t)ra;  // first link of run B: ra < B
+        unroot(B);
       } else {
         const int rb = find_own(par, pb);
-        if (ra < rb) par[rb] = (uint16_t)ra;
-        else if (rb < ra) par[ra] = (uint16_t)rb;
+        if (ra < rb) {
+          par[rb] = (uint16_t)ra;
+          unroot(rb);
+        } else if (rb < ra) {
+          par[ra] = (uint16_t)rb;
+          unroot(ra);
+        }
       }
     }
   }
@@ -695,13 +715,14 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
   }
 
   // ---- tile-local clusters (§2.3)
-  strip_scan<WPR, H>(par, e_int, d_int, wmask, y0r, nv, w);
   // the roots of my strip's components: only these are ever linked below
   uint32_t sroot[H];
 #pragma unroll
+  for (int r = 0; r < H; ++r) sroot[r] = (H == 2 && r == 0 && nv == 1) ? ~(e_int[0] << 1) & wmask : 0u;
+  strip_scan<WPR, H>(par, e_int, d_int, wmask, y0r, nv, w, sroot);
+#pragma unroll
   for (int r = 0; r < H; ++r) {
-    sroot[r] = 0u;
-    if (r >= nv) continue;
+    if (H == 2 || r >= nv) continue;
     const int base = (y0r + r) * TW + 32 * w;
     uint32_t R = ~(e_int[r] << 1) & wmask;
     while (R) {
