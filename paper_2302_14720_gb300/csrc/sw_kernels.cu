@@ -683,12 +683,22 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
       const uint32_t i0 = (uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w);
       if ((L & 1) == 0) {
         // even L: sites i0+b, i0+b+1 (b even) share Philox block (i0+b)/2
+        if (nb == 32) {
+          // a whole word: the pair bits shift in from the top, 2 per block
 #pragma unroll 4
-        for (int b = 0; b < 32; b += 2) {
-          if (b < nb) {
+          for (int b = 0; b < 32; b += 2) {
             const uint4 q = philox4x32_10(make_uint4((i0 + b) >> 1, a.t, 0u, 0u), a.ks);
-            rE |= ((uint32_t)(q.x < a.thr) << b) | ((uint32_t)(q.z < a.thr) << (b + 1));
-            rS |= ((uint32_t)(q.y < a.thr) << b) | ((uint32_t)(q.w < a.thr) << (b + 1));
+            rE = (rE >> 2) | ((uint32_t)(q.x < a.thr) << 30) | ((uint32_t)(q.z < a.thr) << 31);
+            rS = (rS >> 2) | ((uint32_t)(q.y < a.thr) << 30) | ((uint32_t)(q.w < a.thr) << 31);
+          }
+        } else {
+#pragma unroll 4
+          for (int b = 0; b < 32; b += 2) {
+            if (b < nb) {
+              const uint4 q = philox4x32_10(make_uint4((i0 + b) >> 1, a.t, 0u, 0u), a.ks);
+              rE |= ((uint32_t)(q.x < a.thr) << b) | ((uint32_t)(q.z < a.thr) << (b + 1));
+              rS |= ((uint32_t)(q.y < a.thr) << b) | ((uint32_t)(q.w < a.thr) << (b + 1));
+            }
           }
         }
       } else {
