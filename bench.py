@@ -570,12 +570,22 @@ def measure_serving(sw, stream, n_requests: int, capacity_su_s: float, budget_gi
     return summary
 
 
-def sw_source_hash() -> str:
+def code_only(text: str) -> str:
+    """C/CUDA source without its comments and with whitespace runs collapsed,
+    so that the hash below follows the code and not its commentary."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def sw_source_hash(csrc: str | None = None) -> str:
     import hashlib
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2302_14720_gb300", "csrc")
+    csrc = csrc or os.path.join(ROOT, "paper_2302_14720_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(f.encode())
+        h.update(code_only(open(os.path.join(csrc, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

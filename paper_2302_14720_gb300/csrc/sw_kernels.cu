@@ -34,11 +34,14 @@
 //      unites the two slot nodes with 64-bit atomicMin; consecutive edges
 //      joining the same two slots are skipped.
 //  phase 3 (new spins §2.4 + E/M, or canonical labels)
-//    - rebuilds the tile-local clusters from the stored bit masks, takes
-//      each border component's global root (its key is the cluster's
-//      canonical label, C9) and each inner component's own root;
-//    - one Philox block (root, t, 1, 0) per root decides the flip (C6); the
-//      flip mask of a word is built from its runs with a prefix xor;
+//    - receives the tile roots of the run starts by one bulk copy, takes
+//      each border component's decision from its global root (its key is
+//      the cluster's canonical label, C9) and each inner component's from
+//      its own root;
+//    - under the flip rule (C6) the bits of a row word's 32 site indices
+//      come from one Philox block, so all inner roots of the word are
+//      decided by one draw; the flip mask of a word is built from its runs
+//      with a prefix xor;
 //    - writes the new int8 spins, and reduces E and M (C10) in int64 using
 //      the new spins of the halo sites (their old spins from phase 1 and
 //      their clusters' flips);
