@@ -579,11 +579,15 @@ def code_only(text: str) -> str:
     return " ".join(text.split())
 
 
+# The sources that compile into the tiled sweep kernels (phases 1-4).
+TILED_SOURCES = ("sw_kernels.cu", "sw_internal.h", "sw_philox.cuh")
+
+
 def sw_source_hash(csrc: str | None = None) -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = csrc or os.path.join(ROOT, "paper_2302_14720_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in TILED_SOURCES:
         h.update(f.encode())
         h.update(code_only(open(os.path.join(csrc, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]

@@ -130,7 +130,7 @@ int sw_destroy(sw_lattice* h);
  * sweep E and M (C10), and the C11 statistics if enabled, are appended to
  * the device-side trace. Errors: SW_EINVAL (n < 0), SW_ENOMEM (trace
  * growth), SW_ECUDA. Device-side failures are reported by the next call that
- * synchronises. A lattice with L <= 181 and statistics off runs all n
+ * synchronises. A lattice with L <= 144 and statistics off runs all n
  * sweeps in one CTA-sized launch (the whole lattice in shared memory)
  * unless the environment variable SW_TILE_SHAPE was set at sw_create, which
  * keeps it on the tiled path; the results are the same. */

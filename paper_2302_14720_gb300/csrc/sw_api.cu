@@ -347,7 +347,7 @@ int sw_sweep(sw_lattice* h, int32_t n) {
   if (rc != SW_OK) return rc;
   const sw::TileShape ts = sw::shape_of(h->shape);
   (void)ts;
-  if (h->L <= sw::kSmallMaxL && !h->hist_on && !h->tiles_only) {
+  if (h->L <= sw::kSmallSweepMaxL && !h->hist_on && !h->tiles_only) {
     // the whole lattice fits one CTA: all n sweeps in one launch
     sw::SmallArgs s{};
     s.L = h->L;

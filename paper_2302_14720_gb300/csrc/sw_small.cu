@@ -5,14 +5,16 @@
 // One launch runs n sweeps back to back with block barriers between the
 // steps, so a small lattice costs no cross-tile merge and no launch per
 // phase. The steps and their results are those of the tiled path:
-//   bonds (§2.1, C5)  a thread per Philox block (two consecutive sites);
-//   clusters (§2.3)   the two ends of every bond are united, the larger root
-//                     hung under the smaller, so every root is its
-//                     cluster's smallest site (C9);
+//   bonds (§2.1, C5)  a warp per row word, a lane per site, the word's bond
+//                     masks assembled by ballot;
+//   clusters (§2.3)   union-find over runs (stretches of a row word joined
+//                     by east bonds), a lane per bond that joins two runs;
+//                     the larger root is hung under the smaller, so every
+//                     root is its cluster's smallest site (C9);
 //   new spins (§2.4)  the flip bits of all site indices are filled from
 //                     their blocks and each root reads its own (C6), or
 //                     each root draws C6b's fresh spin; a warp per row
-//                     word sets its 32 sites;
+//                     word sets its 32 sites from their runs' roots;
 //   E and M (C10)     from the new bit masks, int64, one trace row per sweep.
 // Spins are read at the start and written back after the last sweep.
 #include <cuda_runtime.h>
@@ -71,8 +73,9 @@ __device__ void small_unite(uint16_t* par, int a, int b, int* err) {
   atomicCAS(err, 0, 1);
 }
 
-__device__ __forceinline__ uint32_t spin_bit(const uint32_t* s, int wpl, int y, int x) {
-  return (s[y * wpl + (x >> 5)] >> (x & 31)) & 1u;
+// Highest run start at or below bit b of a word (R always has bit 0 set).
+__device__ __forceinline__ int small_run_start(uint32_t R, int b) {
+  return 31 - __clz(R & (0xffffffffu >> (31 - b)));
 }
 
 template <typename T>
@@ -94,6 +97,11 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_sweep_kernel(const Sma
   uint32_t* s_dec = s_s + RWN;   // [DW] decision bit of every root
   uint16_t* par = reinterpret_cast<uint16_t*>(s_dec + DW);  // [N]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // lanes per row word for bonds and unions: as many as the threads allow
+  // (a power of two, at most 32), each taking 32 / G consecutive columns
+  int G = 1;
+  while (G < 32 && 2 * G * RWN <= NT) G *= 2;
+  const int PER = 32 / G, sub = lane % G;
 
   for (int rw = warp; rw < RWN; rw += NW) {
     const int y = rw / WPL, x = (rw % WPL) * 32 + lane;
@@ -105,43 +113,81 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_sweep_kernel(const Sma
 
   for (int k = 0; k < a.n; ++k) {
     const uint32_t t = a.t0 + (uint32_t)k;
-    for (int i = tid; i < RWN; i += NT) {
-      s_e[i] = 0u;
-      s_s[i] = 0u;
-    }
     for (int i = tid; i < DW; i += NT) s_dec[i] = 0u;
     for (int i = tid; i < N; i += NT) par[i] = (uint16_t)i;
-    __syncthreads();
 
-    // ---- bonds (§2.1): block (p, t, 0, 0) serves sites 2p and 2p+1 (C5)
-    for (int p = tid; 2 * p < N; p += NT) {
-      const uint4 q = philox4x32_10(make_uint4((uint32_t)p, t, 0u, 0u), a.ks);
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int i = 2 * p + j;
-        if (i >= N) break;
-        const int y = i / L, x = i - y * L;
-        const int xe = x + 1 == L ? 0 : x + 1, ys = y + 1 == L ? 0 : y + 1;
-        const uint32_t si = spin_bit(s_spin, WPL, y, x);
-        const uint32_t we = j ? q.z : q.x, ws = j ? q.w : q.y;
-        const uint32_t bit = 1u << (x & 31);
-        if (si == spin_bit(s_spin, WPL, y, xe) && we < a.thr) atomicOr(&s_e[y * WPL + (x >> 5)], bit);
-        if (si == spin_bit(s_spin, WPL, ys, x) && ws < a.thr) atomicOr(&s_s[y * WPL + (x >> 5)], bit);
+    // ---- bonds (§2.1): G lanes per row word, each drawing a stretch of
+    // 32 / G sites (one block for the two sites of a pair when both lie in
+    // its stretch, C5); the word's masks are or-reduced across the G lanes
+    for (int rw0 = warp * (32 / G); rw0 < RWN; rw0 += NT / G) {
+      const int rw = rw0 + lane / G;
+      uint32_t eb = 0u, sb = 0u;
+      int y = 0, w = 0, nb = 0;
+      if (rw < RWN) {
+        y = rw / WPL;
+        w = rw % WPL;
+        nb = min(32, L - 32 * w);
+        const uint32_t i0 = (uint32_t)(y * L + 32 * w);
+        const int b1 = min(nb, sub * PER + PER);
+        for (int b = sub * PER; b < b1; ++b) {
+          const uint32_t i = i0 + b;
+          const uint4 q = philox4x32_10(make_uint4(i >> 1, t, 0u, 0u), a.ks);
+          if ((i & 1u) == 0u && b + 1 < b1) {  // both sites of the pair
+            eb |= ((uint32_t)(q.x < a.thr) << b) | ((uint32_t)(q.z < a.thr) << (b + 1));
+            sb |= ((uint32_t)(q.y < a.thr) << b) | ((uint32_t)(q.w < a.thr) << (b + 1));
+            ++b;
+          } else {
+            eb |= (uint32_t)(((i & 1u) ? q.z : q.x) < a.thr) << b;
+            sb |= (uint32_t)(((i & 1u) ? q.w : q.y) < a.thr) << b;
+          }
+        }
+      }
+      for (int o = 1; o < G; o <<= 1) {
+        eb |= __shfl_xor_sync(0xffffffffu, eb, o);
+        sb |= __shfl_xor_sync(0xffffffffu, sb, o);
+      }
+      if (rw < RWN && sub == 0) {
+        const uint32_t vm = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
+        const uint32_t sp = s_spin[rw];
+        // east neighbours: the next site in the word; the word's last site
+        // meets the next word's first, or column 0 of its row (periodic)
+        const uint32_t nxt = w + 1 < WPL ? s_spin[rw + 1] : s_spin[y * WPL];
+        const uint32_t sE = ((sp >> 1) & (vm >> 1)) | ((nxt & 1u) << (nb - 1));
+        const uint32_t sS = s_spin[(y + 1 == L ? 0 : y + 1) * WPL + w];
+        s_e[rw] = eb & ~(sp ^ sE) & vm;
+        s_s[rw] = sb & ~(sp ^ sS) & vm;
       }
     }
     __syncthreads();
 
-    // ---- clusters (§2.3)
-    for (int i = tid; i < N; i += NT) {
-      const int y = i / L, x = i - y * L;
-      const int rw = y * WPL + (x >> 5);
-      const uint32_t bit = 1u << (x & 31);
-      if (s_e[rw] & bit) small_unite(par, i, y * L + (x + 1 == L ? 0 : x + 1), a.err);
-      if (s_s[rw] & bit) small_unite(par, i, (y + 1 == L ? 0 : y + 1) * L + x, a.err);
+    // ---- clusters (§2.3) over runs: a run is a stretch of a row word
+    // joined by east bonds inside the word, and its first site is its
+    // union-find node. Unions join the runs that the bonds between words,
+    // across the row's periodic wrap and between rows connect; the larger
+    // node is hung under the smaller, so every root is its cluster's
+    // smallest site (C9: a cluster's smallest site starts a run). G lanes
+    // share a row word, each uniting the bonds of its 32 / G columns in turn.
+    for (int rw = tid / G; rw < RWN; rw += NT / G) {
+      const int y = rw / WPL, w = rw % WPL, nb = min(32, L - 32 * w);
+      const uint32_t vm = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u), lastb = 1u << (nb - 1);
+      const uint32_t mine = (PER == 32 ? 0xffffffffu : ((1u << PER) - 1u)) << (sub * PER);
+      const uint32_t e = s_e[rw], ein = e & ~lastb, R = ~(ein << 1) & vm;
+      const int base = y * L + 32 * w;
+      const int yn = y + 1 == L ? 0 : y + 1, rwn = yn * WPL + w, basen = yn * L + 32 * w;
+      const uint32_t en = s_e[rwn] & ~lastb, Rn = ~(en << 1) & vm, d = s_s[rw];
+      // a south bond is redundant when the one left of it joins the same two runs
+      uint32_t need = d & ~((d & ein & en) << 1) & mine;
+      while (need) {
+        const int j = __ffs(need) - 1;
+        need &= need - 1;
+        small_unite(par, base + small_run_start(R, j), basen + small_run_start(Rn, j), a.err);
+      }
+      if ((e & lastb & mine) != 0u)
+        small_unite(par, base + small_run_start(R, nb - 1), w + 1 < WPL ? base + nb : y * L, a.err);
     }
     __syncthreads();
 
-    // ---- every site points at its root; roots draw their decision. Flip
+    // ---- every run start points at its root; roots draw their decision. Flip
     // rule (C6): word k of s_dec, the bits of site indices 32k .. 32k+31, is
     // word k & 3 of block k >> 2, so every word is filled from its block and
     // each root reads its own bit. Assignment rule (C6b): the roots are
@@ -163,13 +209,17 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_sweep_kernel(const Sma
         const int i = i0 + lane;
         bool isroot = false;
         if (i < N) {
-          int r = i, p = par[r];
-          while (p != r) {
-            r = p;
-            p = par[r];
+          const int y = i / L, x = i - y * L;
+          const bool starts = (x & 31) == 0 || !((s_e[y * WPL + (x >> 5)] >> ((x & 31) - 1)) & 1u);
+          if (starts) {
+            int r = i, p = par[r];
+            while (p != r) {
+              r = p;
+              p = par[r];
+            }
+            par[i] = (uint16_t)r;  // concurrent stores all write roots
+            isroot = r == i && !flip_rule;
           }
-          par[i] = (uint16_t)r;  // concurrent stores all write roots
-          isroot = r == i && !flip_rule;
         }
         const uint32_t m = __ballot_sync(0xffffffffu, isroot);
         if (isroot) q[(qh + qn + __popc(m & ((1u << lane) - 1u))) & 63] = (uint16_t)i;
@@ -190,12 +240,15 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_sweep_kernel(const Sma
     }
     __syncthreads();
 
-    // ---- new spins (§2.4): a warp per row word, a lane per site
+    // ---- new spins (§2.4): a warp per row word, a lane per site, each site
+    // taking the decision of its run's root
     for (int rw = warp; rw < RWN; rw += NW) {
-      const int y = rw / WPL, x = (rw % WPL) * 32 + lane;
+      const int y = rw / WPL, w = rw % WPL, nb = min(32, L - 32 * w);
       bool d = false;
-      if (x < L) {
-        const int r = par[y * L + x];
+      if (lane < nb) {
+        const uint32_t vm = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
+        const uint32_t R = ~((s_e[rw] & ~(1u << (nb - 1))) << 1) & vm;
+        const int r = par[y * L + 32 * w + small_run_start(R, lane)];
         d = (s_dec[r >> 5] >> (r & 31)) & 1u;
       }
       const uint32_t dm = __ballot_sync(0xffffffffu, d);

@@ -87,9 +87,11 @@ def test_batch_mixed_rules(sw):
 # ------------------------------------------------ whole-lattice CTA path
 
 @pytest.mark.parametrize("rule", ["flip", "assign"])
-@pytest.mark.parametrize("L", [2, 3, 5, 17, 31, 32, 33, 64, 100, 128, 181, 182])
+@pytest.mark.parametrize("L", [2, 3, 5, 17, 31, 32, 33, 64, 100, 128, 144, 145, 181])
 def test_small_lattice_path_parity(sw, L, rule):
-    # L <= 181 runs every sweep of a call in one CTA; 182 is the first tiled size
+    # sw_sweep runs every sweep of a call in one CTA for L <= 144; 145 is the
+    # first tiled size (the one-CTA kernel itself goes up to 181: see the
+    # allocation-free entry point's tests)
     beta = [0.3, 0.44068679, 0.6][L % 3]
     seed, n = 4000 + L, 9
     with sw.Lattice(L, beta, seed) as lat:

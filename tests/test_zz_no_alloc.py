@@ -27,7 +27,7 @@ def sw():
     return sw
 
 
-@pytest.mark.parametrize("L,beta", [(5, 0.6), (130, BETA_C), (1000, 0.5), (1024, BETA_C)])
+@pytest.mark.parametrize("L,beta", [(5, 0.6), (130, BETA_C), (181, 0.41), (1000, 0.5), (1024, BETA_C)])
 def test_noalloc_matches_sw_sweep_on_two_calls(sw, L, beta):
     import torch
     seed, t0, n = 4242 + L, 17, 4
