@@ -113,15 +113,10 @@ __device__ __forceinline__ void store_spin_bits(int8_t* p, uint32_t bits, int nb
 // Parents are 16-bit local site indices (par[x] <= x; roots point to
 // themselves).
 
-// Replace the 16-bit entry at p by v if it is larger; returns the old entry.
-__device__ __forceinline__ uint32_t atomic_min_u16(uint16_t* p, uint32_t v) {
-  unsigned short old = *reinterpret_cast<volatile unsigned short*>(p);
-  for (;;) {
-    if (old <= v) return old;
-    const unsigned short seen = atomicCAS(reinterpret_cast<unsigned short*>(p), old, (unsigned short)v);
-    if (seen == old) return old;
-    old = seen;
-  }
+// Hang root a under b if a is still a root: one 16-bit compare-and-swap of
+// par[a] from a to b. Returns the entry found (a on success).
+__device__ __forceinline__ int link_root_u16(uint16_t* par, int a, int b) {
+  return (int)atomicCAS(reinterpret_cast<unsigned short*>(par + a), (unsigned short)a, (unsigned short)b);
 }
 
 // Root of x while no other thread writes the entries on its path (the
@@ -160,9 +155,6 @@ __device__ __forceinline__ int find_final(const volatile uint16_t* par, int x) {
   return x;
 }
 
-// Lock-free union: the larger root is hung under the smaller one; a failed
-// minimum means another thread linked `a` first, and the loop carries on
-// with a's new parent. The cap only guards against corrupted memory.
 // Roots of a and b (as find_shared), the two paths walked side by side so
 // that their loads overlap.
 __device__ __forceinline__ void find_shared2(volatile uint16_t* par, int& a, int& b) {
@@ -183,6 +175,9 @@ __device__ __forceinline__ void find_shared2(volatile uint16_t* par, int& a, int
   }
 }
 
+// Lock-free union: the larger root is hung under the smaller one; a failed
+// link means another thread linked `a` first, and the loop carries on with
+// a's new parent. The cap only guards against corrupted memory.
 __device__ void unite_shared(uint16_t* par, int a, int b, int* err) {
   for (int it = 0; it < kUnionCap; ++it) {
     find_shared2(par, a, b);
@@ -192,9 +187,9 @@ __device__ void unite_shared(uint16_t* par, int a, int b, int* err) {
       a = b;
       b = tmp;
     }
-    const int old = (int)atomic_min_u16(&par[a], (uint32_t)b);
+    const int old = link_root_u16(par, a, b);
     if (old == a) return;
-    a = old;
+    a = old;  // another lane linked a first: carry on from its new parent
   }
   atomicCAS(err, 0, kErrUnionCap);
 }

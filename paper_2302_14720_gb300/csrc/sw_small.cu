@@ -29,19 +29,10 @@ namespace {
 constexpr int kSmallThreads = 1024;
 constexpr int kSmallUnionCap = 1 << 20;
 
-// Replace the 16-bit entry at p by v if it is larger; returns the old entry.
-__device__ __forceinline__ uint32_t small_atomic_min_u16(uint16_t* p, uint32_t v) {
-  unsigned int* w = reinterpret_cast<unsigned int*>(reinterpret_cast<uintptr_t>(p) & ~uintptr_t(3));
-  const int sh = (reinterpret_cast<uintptr_t>(p) & 2u) ? 16 : 0;
-  unsigned int old = *reinterpret_cast<volatile unsigned int*>(w);
-  for (;;) {
-    const uint32_t cur = (old >> sh) & 0xFFFFu;
-    if (cur <= v) return cur;
-    const unsigned int nw = (old & ~(0xFFFFu << sh)) | (v << sh);
-    const unsigned int seen = atomicCAS(w, old, nw);
-    if (seen == old) return cur;
-    old = seen;
-  }
+// Hang root a under b if a is still a root: one 16-bit compare-and-swap of
+// par[a] from a to b. Returns the entry found (a on success).
+__device__ __forceinline__ int small_link_root(uint16_t* par, int a, int b) {
+  return (int)atomicCAS(reinterpret_cast<unsigned short*>(par + a), (unsigned short)a, (unsigned short)b);
 }
 
 // Root of x while other threads may be uniting (path halving).
@@ -66,9 +57,9 @@ __device__ void small_unite(uint16_t* par, int a, int b, int* err) {
       a = b;
       b = tmp;
     }
-    const int old = (int)small_atomic_min_u16(&par[a], (uint32_t)b);
+    const int old = small_link_root(par, a, b);
     if (old == a) return;
-    a = old;
+    a = old;  // another thread linked a first: carry on from its new parent
   }
   atomicCAS(err, 0, 1);
 }
