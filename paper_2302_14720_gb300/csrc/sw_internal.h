@@ -132,8 +132,8 @@ cudaError_t launch_batch_advance(const BatchArgs& b, cudaStream_t st);
 // Whole sweeps of one small lattice in one CTA (sw_small.cu). 181^2 < 2^15,
 // so 16-bit parents index every site.
 constexpr int kSmallMaxL = 181;
-// sw_sweep takes the one-CTA path up to this side; above it the tiled path
-// is the faster one on GB300 (74 vs 65 us per sweep at L = 160).
+// sw_sweep takes the one-CTA path up to this side; from about L = 160 on the
+// tiled path is as fast on GB300 (62 us per sweep either way at L = 160).
 constexpr int kSmallSweepMaxL = 144;
 struct SmallArgs {
   int L;
