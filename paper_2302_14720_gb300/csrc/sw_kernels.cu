@@ -1,6 +1,6 @@
 // sw_kernels.cu -- the Swendsen-Wang sweep on sm_103a.
 //
-// One sweep (paper §2) runs as three kernels over tiles of TW = 32*WPR
+// One sweep (paper §2) runs as three phases (four launches) over tiles of TW = 32*WPR
 // columns by TH rows. Sites are handled as bit masks, 32 per 32-bit word
 // (bit k = site x0+32w+k). Each thread owns one word column w of an H-row
 // strip of the tile and scans it top to bottom.
@@ -17,8 +17,8 @@
 //      reached from two roots merges them (the larger index points to the
 //      smaller). Parents are 16-bit, in shared memory, and owned by the
 //      scanning thread, so the scan needs no atomics. Bonds across strip
-//      boundaries and across words are united afterwards with atomic
-//      minimum (the larger root points to the smaller), so each tile
+//      boundaries and across words are united afterwards, a root linked by
+//      a 16-bit compare-and-swap (the larger root points to the smaller), so each tile
 //      component's root is its smallest site -- the "lowest value label"
 //      of §2.3;
 //    - every tile component that touches the tile border gets a slot; slot
