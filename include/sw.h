@@ -190,6 +190,17 @@ int sw_spins(sw_lattice* h, int8_t* out, int32_t out_is_device);
  * (its start becomes t). Used to resume a run from a checkpoint. */
 int sw_set_state(sw_lattice* h, const int8_t* spins, uint32_t t, int32_t in_is_device);
 
+/* sw_set_state from host memory without waiting: the copy into the staging
+ * buffer, its check and the exchange of buffers are queued on the handle's
+ * stream and the call returns at once, so a host loop can queue the next
+ * state while the GPU still sweeps. spins_host (int8 [L][L]) must stay
+ * unchanged until the stream has copied it (pinned memory makes the copy
+ * asynchronous; pageable memory is copied before the call returns). A value
+ * other than +1/-1 is reported as SW_EINVAL by the next synchronising call,
+ * and the spins are then those from before this call (a kernel copies them
+ * back); the counter is t and the trace starts at t either way. */
+int sw_set_state_async(sw_lattice* h, const int8_t* spins_host, uint32_t t);
+
 /* Debug export of the bonds that the NEXT sweep (counter t) draws from the
  * current spins (§2.1): out_host uint8 [L][L], bit0 = east bond,
  * bit1 = south bond. Synchronises. The state is not changed. */

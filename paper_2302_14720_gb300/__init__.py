@@ -52,6 +52,7 @@ SIGNATURES = {
     "sw_labels_equivalence": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "sw_spins": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "sw_set_state": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_int32]),
+    "sw_set_state_async": (ctypes.c_int, [_P, _P, ctypes.c_uint32]),
     "sw_bonds": (ctypes.c_int, [_P, _P]),
     "sw_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sw_timing_read": (ctypes.c_int, [_P, _P, _P]),
@@ -217,6 +218,14 @@ def sw_set_state(h: int, spins, t: int, in_device_ptr: bool = False) -> None:
         return
     s = np.ascontiguousarray(spins, dtype=np.int8)
     _check(_lib.sw_set_state(h, _host_ptr(s), int(t) & 0xFFFFFFFF, 0), "sw_set_state")
+
+
+def sw_set_state_async(h: int, spins: np.ndarray, t: int) -> None:
+    """spins: C-contiguous int8 host array (pinned for an asynchronous copy); it
+    must stay unchanged until the handle's stream has copied it."""
+    if not (isinstance(spins, np.ndarray) and spins.dtype == np.int8 and spins.flags["C_CONTIGUOUS"]):
+        raise TypeError("sw_set_state_async needs a C-contiguous int8 numpy array (it is read after the call)")
+    _check(_lib.sw_set_state_async(h, _host_ptr(spins), int(t) & 0xFFFFFFFF), "sw_set_state_async")
 
 
 def sw_bonds(h: int, L: int) -> np.ndarray:
@@ -387,6 +396,9 @@ class Lattice:
 
     def set_state(self, spins, t: int) -> None:
         sw_set_state(self.h, spins, t)
+
+    def set_state_async(self, spins: np.ndarray, t: int) -> None:
+        sw_set_state_async(self.h, spins, t)
 
     def close(self) -> None:
         if self.h:

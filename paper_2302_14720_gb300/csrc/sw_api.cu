@@ -464,6 +464,40 @@ int sw_spins(sw_lattice* h, int8_t* out, int32_t out_is_device) {
   return sync_and_check(h);
 }
 
+namespace {
+
+// After an asynchronous host set_state: if the check flagged the new spins,
+// copy the previous state (now in the staging buffer) back. Nothing else is
+// done when the flag is clear, so the launch costs a few microseconds.
+__global__ void restore_if_bad_kernel(int8_t* spins, const int8_t* previous, int64_t n, const int* err) {
+  if (*reinterpret_cast<const volatile int*>(err) != sw::kErrBadSpin) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nv = n / 16;
+  uint4* d = reinterpret_cast<uint4*>(spins);
+  const uint4* s = reinterpret_cast<const uint4*>(previous);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) d[i] = s[i];
+  for (int64_t i = 16 * nv + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) spins[i] = previous[i];
+}
+
+}  // namespace
+
+int sw_set_state_async(sw_lattice* h, const int8_t* spins, uint32_t t) {
+  if (!h || !spins) return fail(SW_EINVAL, "NULL argument");
+  const size_t N = (size_t)h->L * h->L;
+  if (!h->staging) SW_CUDA(cudaMalloc(&h->staging, N), "staging buffer");
+  SW_CUDA(cudaMemsetAsync(h->tb.err, 0, sizeof(int), h->stream), "error flag reset");
+  SW_CUDA(cudaMemcpyAsync(h->staging, spins, N, cudaMemcpyHostToDevice, h->stream), "spins copy");
+  SW_CUDA(sw::launch_check_spins(h->staging, (int64_t)N, h->tb.err, h->stream), "spin check launch");
+  int8_t* previous = h->spins;
+  h->spins = h->staging;
+  h->staging = previous;
+  restore_if_bad_kernel<<<4 * 152, 256, 0, h->stream>>>(h->spins, h->staging, (int64_t)N, h->tb.err);
+  SW_CUDA(cudaGetLastError(), "restore launch");
+  h->t = t;
+  h->t_base = t;
+  return SW_OK;
+}
+
 int sw_set_state(sw_lattice* h, const int8_t* spins, uint32_t t, int32_t in_is_device) {
   if (!h || !spins) return fail(SW_EINVAL, "NULL argument");
   const size_t N = (size_t)h->L * h->L;
