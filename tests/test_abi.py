@@ -62,3 +62,15 @@ def test_no_cpu_fallback(lib):
     with pytest.raises(lib.SWError) as ei:
         lib.sw_create(64, 0.4, 1, 0)
     assert ei.value.status == lib.SW_ECUDA
+
+
+def test_async_set_state_checks_its_host_array(lib):
+    # the array is read after the call returns, so the binding takes only an
+    # int8 C-contiguous numpy array (checked before the library is called)
+    for bad in (np.ones((4, 4), np.int32), np.ones((4, 8), np.int8)[:, ::2], [[1, -1], [1, 1]]):
+        with pytest.raises(TypeError):
+            lib.sw_set_state_async(0, bad, 0)
+    # a NULL handle with a valid array is the library's SW_EINVAL
+    with pytest.raises(lib.SWError) as ei:
+        lib.sw_set_state_async(0, np.ones((4, 4), np.int8), 0)
+    assert ei.value.status == lib.SW_EINVAL
