@@ -80,7 +80,7 @@ def log(*a):
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi samples every 50 ms from construction to stop(); stop()
+    """nvidia-smi samples every 10 ms from construction to stop(); stop()
     reports the samples whose timestamps fall inside the marked window (the
     timed region) and, when the window is shorter than the sampling period,
     the samples of the whole busy span around it."""
@@ -95,7 +95,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -145,7 +145,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(r[1] for r in use) if use else None,
                 "sm_max_mhz": max(r[2] for r in use) if use else None,
                 "samples": len(use), "samples_in_timed_region": len(inside),
-                "sampled": "timed region" if inside else "warm-up through timed region (region shorter than the 50 ms period)",
+                "sampled": "timed region" if inside else "warm-up through timed region (no sample fell inside it)",
                 "reasons": sorted(set().union(*(r[3] for r in use))) if use else []}
 
 
