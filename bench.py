@@ -51,7 +51,8 @@ TW, TH = 128, 64
 NB = 2 * TH + 2 * TW
 BBW = 2 * (TH // 32) + 2 * (TW // 32)
 RW = (TW // 32) * TH  # 32-site row-words per tile
-# Algorithmic bytes per full tile ("Bytes per site"); slot nodes
+# Algorithmic bytes per full tile: what each kernel must read and write for
+# the stored layout (bit masks, 16-bit tile roots, border tables); slot nodes
 # (8 bytes per border component) are data dependent and not counted.
 PHASE_BYTES_PER_TILE = {
     # spins + halo in; spin/east/south masks, 16-bit tile roots, border-root

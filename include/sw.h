@@ -187,7 +187,8 @@ int sw_spins(sw_lattice* h, int8_t* out, int32_t out_is_device);
  * returns SW_EINVAL, leaving the state untouched, if a value is invalid.
  * Device input is copied and checked asynchronously; a bad value is
  * reported as SW_EINVAL by the next synchronising call. Clears the trace
- * (its start becomes t). Used to resume a run from a checkpoint. */
+ * (its start becomes t) and any device error still pending from earlier
+ * calls. Used to resume a run from a checkpoint. */
 int sw_set_state(sw_lattice* h, const int8_t* spins, uint32_t t, int32_t in_is_device);
 
 /* sw_set_state from host memory without waiting: the copy into the staging
@@ -198,7 +199,10 @@ int sw_set_state(sw_lattice* h, const int8_t* spins, uint32_t t, int32_t in_is_d
  * asynchronous; pageable memory is copied before the call returns). A value
  * other than +1/-1 is reported as SW_EINVAL by the next synchronising call,
  * and the spins are then those from before this call (a kernel copies them
- * back); the counter is t and the trace starts at t either way. */
+ * back); the counter is t and the trace starts at t either way. The call
+ * never clears an error that is still pending from earlier work, so queuing
+ * a valid state after an invalid one still ends in SW_EINVAL; a reported
+ * SW_EINVAL of this kind is cleared by the report. */
 int sw_set_state_async(sw_lattice* h, const int8_t* spins_host, uint32_t t);
 
 /* Debug export of the bonds that the NEXT sweep (counter t) draws from the

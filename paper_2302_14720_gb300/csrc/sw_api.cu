@@ -229,7 +229,10 @@ int sync_and_check(sw_lattice* h) {
   switch (flag) {
     case sw::kErrNone: return SW_OK;
     case sw::kErrUnionCap: return fail(SW_ETIMEOUT, "device union-find retry loop reached its cap");
-    case sw::kErrBadSpin: return fail(SW_EINVAL, "sw_set_state: device spins contain values other than +1/-1");
+    case sw::kErrBadSpin:
+      // the state is valid again (the previous spins were kept): report once
+      SW_CUDA(cudaMemset(h->tb.err, 0, sizeof(int)), "error flag reset");
+      return fail(SW_EINVAL, "sw_set_state: spins contain values other than +1/-1");
     case sw::kErrSlotOverflow: return fail(SW_EDEVICE, "device: tile border slots overflowed");
     case sw::kErrCopyTimeout: return fail(SW_ETIMEOUT, "device: a bulk copy into shared memory did not complete");
     default: return fail(SW_EDEVICE, "device error flag %d", flag);
@@ -466,11 +469,16 @@ int sw_spins(sw_lattice* h, int8_t* out, int32_t out_is_device) {
 
 namespace {
 
-// After an asynchronous host set_state: if the check flagged the new spins,
-// copy the previous state (now in the staging buffer) back. Nothing else is
-// done when the flag is clear, so the launch costs a few microseconds.
-__global__ void restore_if_bad_kernel(int8_t* spins, const int8_t* previous, int64_t n, const int* err) {
-  if (*reinterpret_cast<const volatile int*>(err) != sw::kErrBadSpin) return;
+// After an asynchronous host set_state: if this call's check flagged the new
+// spins, copy the previous state (now in the staging buffer) back and raise
+// kErrBadSpin on the handle's error word unless an earlier error is still
+// pending there (first writer wins, so nothing unreported is overwritten).
+// Nothing else is done when the flag is clear, so the launch costs a few
+// microseconds.
+__global__ void restore_if_bad_kernel(int8_t* spins, const int8_t* previous, int64_t n, const int* check,
+                                      int* err) {
+  if (*reinterpret_cast<const volatile int*>(check) == 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(err, 0, sw::kErrBadSpin);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nv = n / 16;
   uint4* d = reinterpret_cast<uint4*>(spins);
@@ -485,13 +493,17 @@ int sw_set_state_async(sw_lattice* h, const int8_t* spins, uint32_t t) {
   if (!h || !spins) return fail(SW_EINVAL, "NULL argument");
   const size_t N = (size_t)h->L * h->L;
   if (!h->staging) SW_CUDA(cudaMalloc(&h->staging, N), "staging buffer");
-  SW_CUDA(cudaMemsetAsync(h->tb.err, 0, sizeof(int), h->stream), "error flag reset");
+  if (!h->check_flag) SW_CUDA(cudaMalloc(&h->check_flag, sizeof(int)), "check flag");
+  // the check runs on a flag of its own: the handle's error word may still
+  // hold an error that no synchronising call has reported yet
+  SW_CUDA(cudaMemsetAsync(h->check_flag, 0, sizeof(int), h->stream), "check flag reset");
   SW_CUDA(cudaMemcpyAsync(h->staging, spins, N, cudaMemcpyHostToDevice, h->stream), "spins copy");
-  SW_CUDA(sw::launch_check_spins(h->staging, (int64_t)N, h->tb.err, h->stream), "spin check launch");
+  SW_CUDA(sw::launch_check_spins(h->staging, (int64_t)N, h->check_flag, h->stream), "spin check launch");
   int8_t* previous = h->spins;
   h->spins = h->staging;
   h->staging = previous;
-  restore_if_bad_kernel<<<4 * 152, 256, 0, h->stream>>>(h->spins, h->staging, (int64_t)N, h->tb.err);
+  restore_if_bad_kernel<<<4 * 152, 256, 0, h->stream>>>(h->spins, h->staging, (int64_t)N, h->check_flag,
+                                                         h->tb.err);
   SW_CUDA(cudaGetLastError(), "restore launch");
   h->t = t;
   h->t_base = t;

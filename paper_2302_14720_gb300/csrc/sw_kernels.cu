@@ -2,39 +2,40 @@
 //
 // One sweep (paper §2) runs as three phases (four launches) over tiles of TW = 32*WPR
 // columns by TH rows. Sites are handled as bit masks, 32 per 32-bit word
-// (bit k = site x0+32w+k). Each thread owns one word column w of an H-row
-// strip of the tile and scans it top to bottom.
+// (bit k = site x0+32w+k). Phase 1 runs one warp per 32-column band of the
+// tile; phase 3 runs one thread per word column of an H-row strip.
 //
 //  phase 1 (bonds §2.1 + tile-local clusters §2.3)
 //    - int8 spins -> sign bits; the tile's east halo column and south halo
 //      row are read too, so every east/south bond of the tile can be drawn;
 //    - Philox-4x32-10 block (site>>1, t, 0, 0) gives the east and south words
 //      of two consecutive sites (C5); bond iff equal spins and word < thr;
-//    - clusters: nodes are word-local runs (maximal stretches of east bonds
-//      inside one word, named by their first site). Inside a strip the
-//      thread scans rows in order, as in Hoshen-Kopelman labelling: a run
-//      with a south bond from the row above takes that run's root, a run
-//      reached from two roots merges them (the larger index points to the
-//      smaller). Parents are 16-bit, in shared memory, and owned by the
-//      scanning thread, so the scan needs no atomics. Bonds across strip
-//      boundaries and across words are united afterwards, a root linked by
-//      a 16-bit compare-and-swap (the larger root points to the smaller), so each tile
-//      component's root is its smallest site -- the "lowest value label"
-//      of §2.3;
+//    - clusters: a Hoshen-Kopelman scan down each 32-column band of the tile,
+//      one warp per band and one lane per column. Runs (maximal stretches of
+//      east bonds inside one row word) take the label of the run above them
+//      that they are bonded to, or their first site as a new label; four bit
+//      masks per row word (row_masks) say which column passes the label down
+//      and which bonds join a second run above, whose labels are then united
+//      (lock-free 16-bit union-find, the larger root under the smaller). Bands
+//      are joined across their east bonds, and every new label is pointed at
+//      its root, the smallest site of the tile component -- the "lowest value
+//      label" of §2.3;
 //    - every tile component that touches the tile border gets a slot; slot
 //      nodes are initialised in a global 64-bit union-find whose entries are
 //      (key << 32 | parent node), key = smallest global site index of the
 //      tile component, so comparing entries compares keys;
 //    - stores the spin/east/south bit masks (12 bytes per 32 sites), the
-//      slot of each border site, the out-going border bonds and the halo
-//      spins (a few hundred bytes per tile).
+//      label of every site (16 bits), the slot of each border site, the
+//      out-going border bonds and the halo spins (a few hundred bytes per
+//      tile).
 //  phase 2 (clusters across tiles, §2.3; device-side, no host round trip
 //    as in §5's maintenance kernel)
 //    - one thread per bonded tile-border edge (including the periodic wrap)
 //      unites the two slot nodes with 64-bit atomicMin; consecutive edges
 //      joining the same two slots are skipped.
 //  phase 3 (new spins §2.4 + E/M, or canonical labels)
-//    - receives the tile roots of the run starts by one bulk copy, takes
+//    - receives the labels of the tile by one bulk copy (a run's root is
+//      the entry of its label), takes
 //      each border component's decision from its global root (its key is
 //      the cluster's canonical label, C9) and each inner component's from
 //      its own root;
@@ -59,13 +60,7 @@ namespace {
 constexpr int kUnionCap = 1 << 20;        // retries of one shared-memory union
 constexpr int kGlobalUnionCap = 1 << 16;  // retries of one global union
 constexpr int kGlobalFindCap = 1 << 20;   // steps of one global find
-constexpr int kFlagClaim = 0x40000000;
 constexpr long long kBulkWaitCycles = 1LL << 31;  // ~1 s at the SM clock: limit of a bulk-copy wait
-
-// Highest run start at or below bit b (R always has bit 0 set for valid b).
-__device__ __forceinline__ int run_start(uint32_t R, int b) {
-  return 31 - __clz(R & (0xffffffffu >> (31 - b)));
-}
 
 // Four int8 spins (+1 = 0x01, -1 = 0xFF) -> four sign bits.
 __device__ __forceinline__ uint32_t sign_bits4(uint32_t w) {
@@ -119,79 +114,49 @@ __device__ __forceinline__ int link_root_u16(uint16_t* par, int a, int b) {
   return (int)atomicCAS(reinterpret_cast<unsigned short*>(par + a), (unsigned short)a, (unsigned short)b);
 }
 
-// Root of x while no other thread writes the entries on its path (the
-// strip scan); halves the path.
-__device__ __forceinline__ int find_own(uint16_t* par, int x) {
-  for (;;) {
-    const int p = par[x];
-    if (p == x) return x;
-    const int gp = par[p];
-    if (gp == p) return p;
-    par[x] = (uint16_t)gp;
-    x = gp;
-  }
-}
 
-// Root of x while other threads may be uniting: path halving with plain
-// 16-bit stores of ancestors (a lost halving store leaves a valid pointer).
-__device__ __forceinline__ int find_shared(volatile uint16_t* par, int x) {
-  for (;;) {
-    const int p = par[x];
-    if (p == x) return x;
-    const int gp = par[p];
-    if (gp == p) return p;
-    par[x] = (uint16_t)gp;
-    x = gp;
-  }
-}
-
-// Root of x once all unions are done: read-only walk.
-__device__ __forceinline__ int find_final(const volatile uint16_t* par, int x) {
-  int p = par[x];
-  while (p != x) {
-    x = p;
-    p = par[x];
-  }
-  return x;
-}
-
-// Roots of a and b (as find_shared), the two paths walked side by side so
-// that their loads overlap.
-__device__ __forceinline__ void find_shared2(volatile uint16_t* par, int& a, int& b) {
-  for (;;) {
+// Lock-free unions of one warp, one pair per lane (lanes with active ==
+// false take part without a pair). Every lane runs the same loop, one step
+// per trip: while a lane's two nodes are not both roots, each moves to its
+// grandparent (path halving, plain 16-bit stores of ancestors); at two
+// distinct roots the larger is hung under the smaller by a 16-bit
+// compare-and-swap, and a failed link (another lane linked that root first)
+// carries on from the root's new parent. The trip condition is decided for
+// the whole warp (__any_sync), so the lanes stay together and a trip costs one
+// pass of the warp, however the lanes' paths differ. The cap only guards
+// against corrupted memory. Every lane of the warp must call this.
+__device__ void unite_warp(uint16_t* par, int a, int b, bool active, int* err) {
+  bool done = !active;
+  for (int it = 0; __any_sync(0xffffffffu, !done); ++it) {
+    if (it >= kUnionCap) {
+      if (!done) atomicCAS(err, 0, kErrUnionCap);
+      break;
+    }
+    if (done) continue;
     const int pa = par[a], pb = par[b];
-    const bool ra = pa == a, rb = pb == b;
-    if (ra && rb) return;
-    const int ga = ra ? a : par[pa];
-    const int gb = rb ? b : par[pb];
-    if (!ra) {
-      if (ga != pa) par[a] = (uint16_t)ga;
-      a = ga;
-    }
-    if (!rb) {
-      if (gb != pb) par[b] = (uint16_t)gb;
-      b = gb;
+    if (pa == a && pb == b) {
+      if (a == b) {
+        done = true;
+      } else {
+        const int hi = max(a, b), lo = min(a, b);
+        const int old = link_root_u16(par, hi, lo);
+        done = old == hi;
+        a = old;  // on failure: the linked root's new parent
+        b = lo;
+      }
+    } else {
+      if (pa != a) {
+        const int ga = par[pa];
+        if (ga != pa) par[a] = (uint16_t)ga;
+        a = ga;
+      }
+      if (pb != b) {
+        const int gb = par[pb];
+        if (gb != pb) par[b] = (uint16_t)gb;
+        b = gb;
+      }
     }
   }
-}
-
-// Lock-free union: the larger root is hung under the smaller one; a failed
-// link means another thread linked `a` first, and the loop carries on with
-// a's new parent. The cap only guards against corrupted memory.
-__device__ void unite_shared(uint16_t* par, int a, int b, int* err) {
-  for (int it = 0; it < kUnionCap; ++it) {
-    find_shared2(par, a, b);
-    if (a == b) return;
-    if (a < b) {
-      const int tmp = a;
-      a = b;
-      b = tmp;
-    }
-    const int old = link_root_u16(par, a, b);
-    if (old == a) return;
-    a = old;  // another lane linked a first: carry on from its new parent
-  }
-  atomicCAS(err, 0, kErrUnionCap);
 }
 
 // ------------------------------------------------------- global union-find
@@ -328,147 +293,54 @@ __device__ __forceinline__ uint32_t last_column_bit(int ncols, int w) {
   return (pl >= 0 && pl < 32) ? (1u << (pl & 31)) : 0u;
 }
 
-// The tile-local clusters of one thread's strip: parents of its sites set
-// to themselves, then the rows scanned top to bottom. e_int/d_int hold the
-// strip's east and south bonds that stay inside the tile. For two-row
-// strips sroot receives the run starts that are still roots (every link
-// clears the bit of the entry it gives a parent); taller strips leave it to
-// the caller.
-template <int WPR, int H>
-__device__ __forceinline__ void strip_scan(uint16_t* par, const uint32_t (&e_int)[H], const uint32_t (&d_int)[H],
-                                           uint32_t vmask, int y0r, int nv, int w, uint32_t (&sroot)[H]) {
-  constexpr int TW = 32 * WPR;
-#pragma unroll
-  for (int r = 0; r < H; ++r) {
-    const int base = (y0r + r) * TW + 32 * w;
-    uint4* p4 = reinterpret_cast<uint4*>(par + base);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t b = (uint32_t)(base + 8 * q);
-      p4[q] = make_uint4(b | ((b + 1) << 16), (b + 2) | ((b + 3) << 16), (b + 4) | ((b + 5) << 16),
-                         (b + 6) | ((b + 7) << 16));
-    }
-  }
-#pragma unroll
-  for (int r = 1; r < H; ++r) {
-    if (r >= nv) break;
-    const uint32_t ep = e_int[r - 1], ec = e_int[r], du = d_int[r - 1];
-    const uint32_t Rp = ~(ep << 1) & vmask, Rc = ~(ec << 1) & vmask;
-    // a south bond at j is redundant when j-1 has one and j-1,j share a run in both rows
-    uint32_t need = du & ~((du & ep & ec) << 1);
-    const int bp = (y0r + r - 1) * TW + 32 * w, bc = bp + TW;
-    if (H == 2) {
-      sroot[0] = Rp;
-      sroot[H - 1] = Rc;
-    }
-    // the entry v (a root of row r-1 or r) gets a parent
-    auto unroot = [&](int v) {
-      if (H == 2) {
-        if (v >= bc) sroot[H - 1] &= ~(1u << (v - bc));
-        else sroot[0] &= ~(1u << (v - bp));
-      }
-    };
-    while (need) {
-      const int j = __ffs(need) - 1;
-      need &= need - 1;
-      const int ra = find_own(par, bp + run_start(Rp, j));
-      const int B = bc + run_start(Rc, j);
-      const int pb = par[B];
-      if (pb == B) {
-        par[B] = (uint16_t)ra;  // first link of run B: ra < B
-        unroot(B);
-      } else {
-        const int rb = find_own(par, pb);
-        if (ra < rb) {
-          par[rb] = (uint16_t)ra;
-          unroot(rb);
-        } else if (rb < ra) {
-          par[ra] = (uint16_t)rb;
-          unroot(ra);
-        }
-      }
-    }
-  }
+// ------------------------------------------------- row masks of the band scan
+//
+// Phase 1 labels a tile by a Hoshen-Kopelman scan down each 32-column band:
+// the rows are visited top to bottom, every run (a maximal stretch of east
+// bonds inside one row word) takes the label of the run above it that it is
+// bonded to, or a new label (its first site) when it has no bond upwards,
+// and a run bonded to several runs above that carry different labels makes
+// those labels equivalent (a union). What each run of a row needs -- which of
+// its columns passes the label down, which columns join a further run above
+// -- follows from four bit masks of the row, computed for all runs of a word
+// at once.
+
+// Bits j of D whose interval (previous bit of D below j, j] holds a bit of X
+// (for the lowest bit of D the interval starts at bit 0). One addition scans
+// all intervals: a bit of X outside D starts a carry that runs up through the
+// bits outside D and stops on the next bit of D.
+__device__ __forceinline__ uint32_t carry_hit(uint32_t X, uint32_t D) {
+  const uint32_t nd = ~D;
+  return ((nd + (X & nd)) & D) | (X & D);
 }
 
-// Bonds leaving a strip: south bonds into its first row from the strip
-// above, and east bonds from each word into the next one. Atomic unions.
-template <int WPR, int TH, int H, int PL>
-__device__ __forceinline__ void strip_joins(uint16_t* par, const uint32_t (&e_int)[H], uint32_t vmask, int y0r,
-                                            int nv, int w, int k, const uint32_t (*s_eint)[WPR],
-                                            const uint32_t (*s_dint)[WPR], uint32_t* q, int* err) {
-  constexpr int TW = 32 * WPR;
-  // The first PL rounds merge strips pairwise without atomics: in round st
-  // the boundary above strip k is joined when k % (2 st) == st, by k's
-  // thread, which then alone touches the 2 st strips of the two groups (trees
-  // do not cross word columns yet). The other boundaries follow with atomics.
-#pragma unroll
-  for (int lv = 0; lv < PL; ++lv) {
-    const int st = 1 << lv;
-    if (k % (2 * st) == st && nv > 0) {
-      const uint32_t ep = s_eint[y0r - 1][w], du = s_dint[y0r - 1][w], ec = e_int[0];
-      const uint32_t Rp = ~(ep << 1) & vmask, Rc = ~(ec << 1) & vmask;
-      uint32_t need = du & ~((du & ep & ec) << 1);
-      const int bp = (y0r - 1) * TW + 32 * w, bc = bp + TW;
-      while (need) {
-        const int j = __ffs(need) - 1;
-        need &= need - 1;
-        const int ra = find_own(par, bp + run_start(Rp, j)), rb = find_own(par, bc + run_start(Rc, j));
-        if (ra < rb) par[rb] = (uint16_t)ra;
-        else if (rb < ra) par[ra] = (uint16_t)rb;
-      }
-    }
-    __syncthreads();
-  }
-  // The remaining joins are atomic unions. The lanes of a warp walk their
-  // bonds in step and queue the pairs to unite (q: the warp's 64 entries,
-  // both ends packed in 16 bits each); the queue is taken 32 pairs at a
-  // time, so every lane unites instead of idling behind the busiest one.
-  const int lane = threadIdx.x & 31;
-  int qh = 0, qn = 0;  // the same in every lane of the warp
-  auto push = [&](bool have, uint32_t pair) {
-    const uint32_t m = __ballot_sync(0xffffffffu, have);
-    if (have) q[(qh + qn + __popc(m & ((1u << lane) - 1u))) & 63] = pair;
-    qn += __popc(m);
-    __syncwarp();
-    if (qn >= 32) {
-      const uint32_t v = q[(qh + lane) & 63];
-      unite_shared(par, (int)(v & 0xFFFFu), (int)(v >> 16), err);
-      qh += 32;
-      qn -= 32;
-      __syncwarp();
-    }
-  };
-  uint32_t need = 0u, Rp = 0u, Rc = 0u;
-  int bp = 0, bc = 0;
-  if (y0r > 0 && nv > 0 && (k % (1 << PL)) == 0) {
-    const uint32_t ep = s_eint[y0r - 1][w], du = s_dint[y0r - 1][w], ec = e_int[0];
-    Rp = ~(ep << 1) & vmask;
-    Rc = ~(ec << 1) & vmask;
-    need = du & ~((du & ep & ec) << 1);
-    bp = (y0r - 1) * TW + 32 * w;
-    bc = bp + TW;
-  }
-  while (__any_sync(0xffffffffu, need != 0u)) {
-    const bool have = need != 0u;
-    uint32_t pair = 0u;
-    if (have) {
-      const int j = __ffs(need) - 1;
-      need &= need - 1;
-      pair = (uint32_t)(bp + run_start(Rp, j)) | ((uint32_t)(bc + run_start(Rc, j)) << 16);
-    }
-    push(have, pair);
-  }
-#pragma unroll
-  for (int r = 0; r < H; ++r) {
-    const bool have = r < nv && ((e_int[r] >> 31) & 1u);
-    const int base = (y0r + r) * TW + 32 * w;
-    push(have, have ? (uint32_t)(base + run_start(~(e_int[r] << 1), 31)) | ((uint32_t)(base + 32) << 16) : 0u);
-  }
-  if (lane < qn) {
-    const uint32_t v = q[(qh + lane) & 63];
-    unite_shared(par, (int)(v & 0xFFFFu), (int)(v >> 16), err);
-  }
+// Masks of row word B given the row word A above it in the same band. eB, eA:
+// east bonds inside the tile (bit 31 = bond into the next word, not part of a
+// run here); vB, vA: valid columns; D: south bonds from A into B.
+//   R: run starts of B;
+//   F: the first column of each run of B with a bond upwards -- the run takes
+//      the label of the site above that column;
+//   S: F, plus the start of every run with no bond upwards (a new label);
+//   M: the other bonds upwards that reach a run of A different from the one
+//      reached by the previous bond of the same run of B -- each asks for a
+//      union of that run's label with the label of the run of B.
+struct RowMasks {
+  uint32_t R, S, F, M;
+};
+__device__ __forceinline__ RowMasks row_masks(uint32_t eB, uint32_t vB, uint32_t eA, uint32_t vA, uint32_t D) {
+  const uint32_t RB = ~(eB << 1) & vB;
+  const uint32_t RA = ~(eA << 1) & vA;
+  const uint32_t F = carry_hit(RB, D);
+  const uint32_t M = carry_hit(RA, D) & ~F;
+  // runs of B that hold a bit of D: the same scan on the reversed word, where
+  // a run's start is the top of its interval
+  const uint32_t withD = __brev(carry_hit(__brev(D), __brev(RB)));
+  RowMasks m;
+  m.R = RB;
+  m.F = F;
+  m.M = M;
+  m.S = F | (RB & ~withD);
+  return m;
 }
 
 template <typename T>
@@ -590,29 +462,57 @@ __device__ __forceinline__ bool cta_args(const SweepArgs& a0, const BatchArgs& b
 
 // ================================================================ phase 1
 
-// Two-row strips keep few values live, so phases 1 and 3 of those shapes ask
-// for 1280 resident threads an SM (at most 51 registers a thread; ten CTAs
-// of 128 threads also fit their ~22 KB of shared memory). Taller strips
-// would spill under that bound and keep the compiler's choice.
+// Phase 3 runs strips of H rows; with two-row strips it asks for 1280
+// resident threads an SM (at most 51 registers a thread; ten CTAs of 128
+// threads also fit their shared memory). Taller strips would spill under that
+// bound and keep the compiler's choice.
 template <int NT, int H>
 constexpr int strip_min_blocks() {
   return H == 2 ? 1280 / NT : 1;
 }
 
-template <int WPR, int TH, int H, int PL, bool BATCH>
-__global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H), H>())
+// Phase 1 runs one warp per 32-column band: 1280 resident threads an SM.
+template <int NT>
+constexpr int band_min_blocks() {
+  return 1280 / NT > 0 ? 1280 / NT : 1;
+}
+
+// One CTA per tile, one warp per 32-column band (word column) of it.
+//  1. spins -> sign bits, halo, bonds (§2.1): row words handed out so that
+//     consecutive threads read consecutive 32-site words of a row;
+//  2. row masks (row_masks) of every row of the band, one lane per row;
+//  3. the scan (§2.3): the warp walks the band's rows top to bottom, lane l
+//     holding column l; per row each lane finds its run's start and the
+//     column that names the run (S), and reads the label from that column's
+//     lane: the label of the site above it (F) or that site's own index (a
+//     new label). Labels are tile-local site indices, so the smaller of two
+//     equivalent labels is the smaller site. Every site's label is stored in
+//     par[]; a new label's entry (par[x] = x) is a union-find root;
+//  4. the unions: each bond of M (its two sites carry the labels to unite)
+//     and each east bond across a band border, by a lock-free union run by
+//     all lanes of a warp together (unite_warp: the larger root hung under
+//     the smaller); then every new label is pointed at its root, so that
+//     par[par[x]] is the root of site x, the component's smallest site -- the
+//     "lowest value label" of §2.3;
+//  5. border components get slots and global nodes, as the cross-tile merge
+//     (phase 2) needs them; par, the masks and the tables go to global memory.
+template <int WPR, int TH, int H, bool BATCH>
+__global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
     phase1_kernel(const SweepArgs a0, const BatchArgs bat) {
   using T = Tile<WPR, TH, H>;
-  constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
-  __shared__ __align__(16) uint16_t par[TH * TW];
+  constexpr int TW = T::TW, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
+  constexpr int NT = 32 * WPR;  // threads of phase 1
+  constexpr int RPL = TH / 32;  // rows per lane
+  static_assert(TH % 32 == 0, "whole warps of rows");
+  __shared__ __align__(16) uint16_t par[TH * TW];  // label of every site; a label's entry is its union-find parent
   __shared__ uint32_t s_spin[TH][WPR];  // the spin bits while drawing bonds, then the border-root marks
   __shared__ uint32_t s_eint[TH][WPR];
   __shared__ uint32_t s_dint[TH][WPR];
   __shared__ uint32_t s_bb[BBW];
   __shared__ int16_t s_broot[NB];
-  uint32_t* const s_bmask = &s_spin[0][0];  // border roots (RW words), once the bonds are drawn
-  __shared__ uint32_t s_pre[RW];     // prefix counts of s_bmask
+  __shared__ uint32_t s_pre[RW];  // prefix counts of s_bmask
   __shared__ uint32_t s_wsum[33];
+  uint32_t* const s_bmask = &s_spin[0][0];  // border roots (RW words), once the bonds are drawn
 
   SweepArgs a;
   int tile;
@@ -620,9 +520,7 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
   const Geometry& g = a.g;
   const int L = g.L;
   const TilePos P = tile_pos<TW, TH>(g, tile);
-  const int tid = threadIdx.x, w = tid % WPR, k = tid / WPR, y0r = k * H;
-  const int lane = tid & 31, warp0 = tid & ~31;
-  const int nv = max(0, min(H, P.nrows - y0r));  // valid rows of my strip
+  const int tid = threadIdx.x, lane = tid & 31, warp0 = tid & ~31;
   uint32_t* eout = s_bb + T::OFF_EOUT;
   uint32_t* sout = s_bb + T::OFF_SOUT;
   uint32_t* hE = s_bb + T::OFF_HE;
@@ -630,16 +528,15 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
 
   for (int i = tid; i < BBW; i += NT) s_bb[i] = 0u;
 
-  // ---- spins of my strip
-  const int nb = max(0, min(32, P.ncols - 32 * w));
-  const uint32_t wmask = word_mask(P.ncols, w);
-  uint32_t s[H];
+  // ---- spins: thread tid takes row words tid, tid + NT, ... (row-major)
 #pragma unroll
-  for (int r = 0; r < H; ++r) {
-    s[r] = 0u;
-    if (r < nv && wmask)
-      s[r] = load_spin_bits(a.spins_in + (size_t)(P.y0 + y0r + r) * L + P.x0 + 32 * w, nb, g.aligned16);
-    s_spin[y0r + r][w] = s[r];
+  for (int i = 0; i < RPL; ++i) {
+    const int rw = tid + NT * i, y = rw / WPR, w = rw % WPR;
+    const int nbw = max(0, min(32, P.ncols - 32 * w));
+    uint32_t sb = 0u;
+    if (y < P.nrows && nbw)
+      sb = load_spin_bits(a.spins_in + (size_t)(P.y0 + y) * L + P.x0 + 32 * w, nbw, g.aligned16);
+    s_spin[y][w] = sb;
   }
   __syncthreads();
 
@@ -658,24 +555,24 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
   }
   __syncthreads();
 
-  // ---- bonds (§2.1)
-  const uint32_t lbit = last_column_bit(P.ncols, w);  // nonzero iff my word holds the tile's last column
-  const bool lastword = lbit != 0u;
-  uint32_t e_int[H], d_int[H];
+  // ---- bonds (§2.1), same row words as the spins
   uint32_t* tb = a.tb.tbits + (size_t)P.tile * 3 * RW;
 #pragma unroll
-  for (int r = 0; r < H; ++r) {
-    const int y = y0r + r;
-    const uint32_t vmask = r < nv ? wmask : 0u;
+  for (int i = 0; i < RPL; ++i) {
+    const int rw = tid + NT * i, y = rw / WPR, w = rw % WPR;
+    const int nb = max(0, min(32, P.ncols - 32 * w));
+    const uint32_t vmask = y < P.nrows ? word_mask(P.ncols, w) : 0u;
+    const uint32_t lbit = last_column_bit(P.ncols, w);  // nonzero iff this word holds the tile's last column
+    const uint32_t s = s_spin[y][w];
     uint32_t sE;
-    if (lastword) {
+    if (lbit) {
       const uint32_t hb = (hE[y >> 5] >> (y & 31)) & 1u;
-      sE = ((s[r] >> 1) & (lbit - 1u)) | (hb ? lbit : 0u);
+      sE = ((s >> 1) & (lbit - 1u)) | (hb ? lbit : 0u);
     } else {
-      sE = (s[r] >> 1) | ((w + 1 < WPR) ? (s_spin[y][w + 1] << 31) : 0u);
+      sE = (s >> 1) | ((w + 1 < WPR) ? (s_spin[y][w + 1] << 31) : 0u);
     }
-    const uint32_t sS = (y + 1 < P.nrows) ? (r + 1 < H ? s[r + 1] : s_spin[y + 1][w]) : hS[w];
-    const uint32_t eqE = ~(s[r] ^ sE) & vmask, eqS = ~(s[r] ^ sS) & vmask;
+    const uint32_t sS = (y + 1 < P.nrows) ? s_spin[y + 1][w] : hS[w];
+    const uint32_t eqE = ~(s ^ sE) & vmask, eqS = ~(s ^ sS) & vmask;
     uint32_t rE = 0, rS = 0;
     if (vmask) {
       const uint32_t i0 = (uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w);
@@ -710,87 +607,128 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
       }
     }
     const uint32_t e = eqE & rE, d = eqS & rS;
-    e_int[r] = e & ~lbit;
-    d_int[r] = (y + 1 < P.nrows) ? d : 0u;
-    s_eint[y][w] = e_int[r];
-    s_dint[y][w] = d_int[r];
-    if (r < nv && (e & lbit)) atomicOr(&eout[y >> 5], 1u << (y & 31));
-    if (r < nv && y == P.nrows - 1) sout[w] = d;
-    const int rw = y * WPR + w;
-    tb[rw] = s[r];
+    s_eint[y][w] = e & ~lbit;
+    s_dint[y][w] = (y + 1 < P.nrows) ? d : 0u;
+    if (vmask && (e & lbit)) atomicOr(&eout[y >> 5], 1u << (y & 31));
+    if (vmask && y == P.nrows - 1) sout[w] = d;
+    tb[rw] = s;
     tb[RW + rw] = e;
     tb[2 * RW + rw] = d;
   }
-
-  // ---- tile-local clusters (§2.3)
-  // the roots of my strip's components: only these are ever linked below
-  uint32_t sroot[H];
-#pragma unroll
-  for (int r = 0; r < H; ++r) sroot[r] = (H == 2 && r == 0 && nv == 1) ? ~(e_int[0] << 1) & wmask : 0u;
-  strip_scan<WPR, H>(par, e_int, d_int, wmask, y0r, nv, w, sroot);
-#pragma unroll
-  for (int r = 0; r < H; ++r) {
-    if (H == 2 || r >= nv) continue;
-    const int base = (y0r + r) * TW + 32 * w;
-    uint32_t R = ~(e_int[r] << 1) & wmask;
-    while (R) {
-      const int b = __ffs(R) - 1;
-      R &= R - 1;
-      if (par[base + b] == base + b) sroot[r] |= 1u << b;
-    }
-  }
   __syncthreads();
   for (int i = tid; i < RW; i += NT) s_bmask[i] = 0u;  // the spin bits are no longer needed
-  // s_pre is free until the border slots: it holds the warps' join queues
-  static_assert((NT / 32) * 64 <= RW, "join queues fit in s_pre");
-  strip_joins<WPR, TH, H, PL>(par, e_int, wmask, y0r, nv, w, k, s_eint, s_dint, s_pre + (tid >> 5) * 64, a.tb.err);
-  __syncthreads();
 
-  // the joins leave chains of strip roots (a strip's root hung under the
-  // root of the strip above, and so on). Pointer jumping over the strip
-  // roots, each round replacing every parent by its parent's parent, points
-  // all of them at their tile roots in a logarithmic number of rounds; only
-  // a strip root's owner writes it, and every value written is an ancestor.
-  // A strip root whose parent is a root is done for good (the joins are
-  // over), so each round only visits the ones still pending.
-  for (int round = 0; round < 64; ++round) {
-    bool changed = false;
+  // ---- row masks of my band: warp w = word column w, lane l holds rows l + 32 j
+  const int w = tid >> 5;
+  const uint32_t wmask = word_mask(P.ncols, w);
+  uint32_t mR[RPL], mS[RPL], mF[RPL], mM[RPL];
 #pragma unroll
-    for (int r = 0; r < H; ++r) {
-      const int base = (y0r + r) * TW + 32 * w;
-      uint32_t R = sroot[r];
-      while (R) {
-        const int b = __ffs(R) - 1;
-        R &= R - 1;
-        const int x = base + b;
-        const int p = par[x], pp = par[p];
-        if (pp != p) {
-          par[x] = (uint16_t)pp;
-          changed = true;
-        } else {
-          sroot[r] &= ~(1u << b);
-        }
-      }
+  for (int j = 0; j < RPL; ++j) {
+    const int y = lane + 32 * j;
+    mR[j] = mS[j] = mF[j] = mM[j] = 0u;
+    if (y < P.nrows && wmask) {
+      const uint32_t eA = y > 0 ? s_eint[y - 1][w] : 0u, D = y > 0 ? s_dint[y - 1][w] : 0u;
+      const RowMasks m = row_masks(s_eint[y][w], wmask, eA, y > 0 ? wmask : 0u, D);
+      mR[j] = m.R;
+      mS[j] = m.S;
+      mF[j] = m.F;
+      mM[j] = m.M;
     }
-    if (!__syncthreads_or(changed)) break;
   }
 
-  // every run start of my strip points at its tile root. Most run starts
-  // are at most two hops from it (parent and grandparent read back to
-  // back); longer paths finish through find_final.
-  uint32_t rootbits[H];  // run starts that are tile roots
+  // ---- the scan (§2.3) down my band, lane = column: label propagation only;
+  // the unions that M asks for are done afterwards from the stored labels
+  if (wmask) {  // the same in every lane of the warp
+    const uint32_t le = 0xffffffffu >> (31 - lane);  // bits 0..lane
+    uint32_t lab = 0u;                                // label of my column's site in the row above
+    int own = 32 * w + lane;                          // my column's site in the current row
 #pragma unroll
-  for (int r = 0; r < H; ++r) {
-    rootbits[r] = 0u;
-    if (r >= nv) continue;
-    const int base = (y0r + r) * TW + 32 * w;
-    uint32_t R = ~(e_int[r] << 1) & wmask;
-    while (R) {
-      const int b = __ffs(R) - 1;
-      R &= R - 1;
-      const int x = base + b, p = par[x], pp = par[p];
-      if (p == x) rootbits[r] |= 1u << b;
-      par[x] = (uint16_t)(pp == p ? p : find_final(par, pp));
+    for (int j = 0; j < RPL; ++j) {
+      const int rows = min(32, P.nrows - 32 * j);
+#pragma unroll 4
+      for (int yy = 0; yy < rows; ++yy) {
+        const uint32_t R = __shfl_sync(0xffffffffu, mR[j], yy);
+        const uint32_t S = __shfl_sync(0xffffffffu, mS[j], yy);
+        const uint32_t F = __shfl_sync(0xffffffffu, mF[j], yy);
+        const int s = 31 - __clz(R & le);                   // start of my run (bit 0 is always a start)
+        const int src = __ffs(S & (0xffffffffu << s)) - 1;  // the column that names my run
+        const uint32_t v = ((F >> lane) & 1u) ? lab : (uint32_t)own;
+        lab = __shfl_sync(0xffffffffu, v, src);
+        par[own] = (uint16_t)lab;
+        own += TW;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- unions: every bond of M (the site above and the site below it carry
+  // labels of two runs that M says may differ) and every east bond across a
+  // band border. Each lane works through its own list -- the M bits of its
+  // rows, then its band border bonds -- one union per warp-wide trip.
+  {
+    uint32_t todo[RPL];
+    uint32_t cross = 0u;  // bit j: row lane + 32 j has an east bond into the next band
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+      todo[j] = mM[j];
+      const int y = lane + 32 * j;
+      if (w + 1 < WPR && y < P.nrows && (s_eint[y][w] >> 31)) cross |= 1u << j;
+    }
+    for (;;) {
+      int xa = 0, xb = 0;
+      bool have = false;
+#pragma unroll
+      for (int j = 0; j < RPL; ++j) {
+        if (!have && todo[j]) {
+          const int b = __ffs(todo[j]) - 1;
+          todo[j] &= todo[j] - 1;
+          xb = (lane + 32 * j) * TW + 32 * w + b;  // site of row lane + 32 j, bonded to the site above
+          xa = xb - TW;
+          have = true;
+        }
+      }
+      if (!have && cross) {
+        const int j = __ffs(cross) - 1;
+        cross &= cross - 1;
+        xa = (lane + 32 * j) * TW + 32 * w + 31;  // last column of my word, bonded to the next word's first
+        xb = xa + 1;
+        have = true;
+      }
+      if (!__any_sync(0xffffffffu, have)) break;
+      unite_warp(par, xa, xb, have, a.tb.err);
+    }
+  }
+  __syncthreads();
+
+  // ---- every new label points at its root; roots recorded for phase 3
+  {
+    uint32_t* rb = a.tb.rbits + (size_t)P.tile * RW;
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+      const int y = lane + 32 * j, base = y * TW + 32 * w;
+      uint32_t NL = mS[j] & ~mF[j], roots = 0u;
+      // warp-wide trips (see unite_warp); a lane out of labels walks from
+      // site 0, which is always a root
+      while (__any_sync(0xffffffffu, NL != 0u)) {
+        int b = -1, r = 0;
+        if (NL) {
+          b = __ffs(NL) - 1;
+          NL &= NL - 1;
+          r = base + b;
+        }
+        int p = par[r];
+        while (__any_sync(0xffffffffu, p != r)) {
+          if (p != r) {
+            r = p;
+            p = par[r];
+          }
+        }
+        if (b >= 0) {
+          if (r == base + b) roots |= 1u << b;
+          else par[base + b] = (uint16_t)r;
+        }
+      }
+      rb[y * WPR + w] = roots;
     }
   }
   __syncthreads();
@@ -799,7 +737,7 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
   for (int j = tid; j < NB; j += NT) {
     int y, x, r = -1;
     if (border_site<TW, TH>(P, j, y, x)) {
-      r = par[y * TW + (x & ~31) + run_start(~(s_eint[y][x >> 5] << 1), x & 31)];
+      r = par[par[y * TW + x]];
       atomicOr(&s_bmask[r >> 5], 1u << (r & 31));
     }
     s_broot[j] = (int16_t)r;
@@ -831,20 +769,13 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
     const int r = s_broot[j];
     bs[j] = r >= 0 ? (uint16_t)slot_of(s_bmask, s_pre, r) : (uint16_t)0xFFFFu;
   }
-  // roots and border marks of my strip for phase 3
+  // labels (a root in every new label's entry) and border marks for phase 3
   {
-    uint16_t* rt = a.tb.roots + (size_t)P.tile * (TW * TH);
+    const uint4* src = reinterpret_cast<const uint4*>(par);
+    uint4* dst = reinterpret_cast<uint4*>(a.tb.roots + (size_t)P.tile * (TW * TH));
+    for (int i = tid; i < TW * TH / 8; i += NT) dst[i] = src[i];
     uint32_t* bm = a.tb.bmask + (size_t)P.tile * RW;
-#pragma unroll
-    for (int r = 0; r < H; ++r) {
-      const int base = (y0r + r) * TW + 32 * w;
-      const uint4* src = reinterpret_cast<const uint4*>(par + base);
-      uint4* dst = reinterpret_cast<uint4*>(rt + base);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) dst[q] = src[q];
-      bm[(y0r + r) * WPR + w] = s_bmask[(y0r + r) * WPR + w];
-      a.tb.rbits[(size_t)P.tile * RW + (y0r + r) * WPR + w] = rootbits[r];
-    }
+    for (int i = tid; i < RW; i += NT) bm[i] = s_bmask[i];
   }
   for (int i = tid; i < BBW; i += NT) a.tb.bbits[(size_t)P.tile * BBW + i] = s_bb[i];
   if (tid == 0) {
@@ -951,7 +882,7 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
   using T = Tile<WPR, TH, H>;
   constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
   constexpr bool HIST = MODE == 1, LABELS = MODE == 2;
-  __shared__ __align__(16) uint16_t par[TH * TW];  // tile root of every run start (from phase 1)
+  __shared__ __align__(16) uint16_t par[TH * TW];  // labels from phase 1: par[par[x]] is the tile root of x
   __shared__ uint32_t s_bmask[RW];                 // border roots
   __shared__ uint32_t s_pre[RW];
   __shared__ uint32_t s_wsum[33];
@@ -1100,7 +1031,7 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
     while (R) {
       const int b = __ffs(R) - 1;
       R &= R - 1;
-      const int rt = par[base + b];
+      const int rt = par[par[base + b]];  // the run's label, then the label's root
       if (LABELS) {
         const int nxt = R ? (__ffs(R) - 1) : nb;
         int key;
@@ -1340,7 +1271,7 @@ cudaError_t launch_all(int which, const SweepArgs& a, int mode, uint8_t* out, cu
   const int ntiles = batch ? batch_tiles : a.g.tiles_x * a.g.tiles_y;
   switch (which) {
     case 1:
-      phase1_kernel<WPR, TH, H, PL, false><<<ntiles, T::NT, 0, st>>>(a, BatchArgs{});
+      phase1_kernel<WPR, TH, H, false><<<ntiles, 32 * WPR, 0, st>>>(a, BatchArgs{});
       break;
     case 2:
       phase2_kernel<WPR, TH, H, false><<<ntiles, TH + T::TW, 0, st>>>(a, BatchArgs{});
@@ -1364,7 +1295,7 @@ cudaError_t launch_all(int which, const SweepArgs& a, int mode, uint8_t* out, cu
       }
       break;
     case 11:
-      phase1_kernel<WPR, TH, H, PL, true><<<ntiles, T::NT, 0, st>>>(a, *batch);
+      phase1_kernel<WPR, TH, H, true><<<ntiles, 32 * WPR, 0, st>>>(a, *batch);
       break;
     case 12:
       phase2_kernel<WPR, TH, H, true><<<ntiles, TH + T::TW, 0, st>>>(a, *batch);

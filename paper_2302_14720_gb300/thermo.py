@@ -1,9 +1,9 @@
 """Temperature scans: energy, specific heat and magnetisation against
-temperature (the quantities the paper plots in §3), measured by running one
+temperature (the quantities the paper plots in §4, Results), measured by running one
 Swendsen-Wang chain per (temperature, seed) together in one sw_batch.
 
 Per temperature, from the per-sweep traces after `n_equil` sweeps:
-  e   = <E> / N                         energy per site (§2.4's H, J = 1)
+  e   = <E> / N                         energy per site (the Hamiltonian that closes §2, J = 1)
   c   = beta^2 (<E^2> - <E>^2) / N      specific heat per site
   m   = <|M|> / N                       magnetisation per site
   chi = beta (<M^2> - <|M|>^2) / N      susceptibility per site

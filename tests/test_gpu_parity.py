@@ -117,8 +117,9 @@ def test_histogram_parity_small(sw, shape, L):
 
 
 def test_config_L1024_cold_histogram(sw):
-    # L=1024, beta_c, cold start, seed 2: E, M and cluster statistics per sweep.
-    L, beta, seed, n = 1024, BETA_C, 2, 30
+    # L=1024, beta_c, cold start, seed 2: E, M and cluster statistics of each
+    # of the first 1000 sweeps (the oracle needs about a minute).
+    L, beta, seed, n = 1024, BETA_C, 2, 1000
     with make(sw, L, beta, seed, init=1) as lat:
         lat.histogram(True)
         lat.sweep(n)

@@ -66,6 +66,29 @@ def test_async_state_rejects_an_invalid_value_and_keeps_the_spins(sw):
         assert np.array_equal(lat.spins(), want_s)
 
 
+def test_a_pending_bad_state_survives_a_second_async_call(sw):
+    """An invalid state queued first and a valid one queued right after: the
+    second call must not wipe the first one's error, so the next synchronising
+    call still reports SW_EINVAL; the valid state is then in place."""
+    L, seed = 64, 4
+    with sw.Lattice(L, 0.45, seed) as lat:
+        lat.sweep(1)
+        bad = np.ones((L, L), np.int8)
+        bad[0, 0] = 0
+        good = random_spins(L, seed=11)
+        lat.set_state_async(bad, 3)
+        lat.set_state_async(good, 5)
+        with pytest.raises(sw.SWError) as ei:
+            lat.spins()
+        assert ei.value.status == sw.SW_EINVAL
+        assert np.array_equal(lat.spins(), good)   # reported once; the valid state stands
+        lat.sweep(2)
+        want_s, want_E, want_M, _ = oracle.run(L, 0.45, seed, 2, spins=good, t0=5)
+        E, M = lat.observables(5, 2)
+        assert np.array_equal(lat.spins(), want_s)
+        assert np.array_equal(E, want_E) and np.array_equal(M, want_M)
+
+
 def test_async_state_needs_an_int8_array(sw):
     with sw.Lattice(16, 0.4, 1) as lat:
         with pytest.raises(TypeError):
