@@ -35,10 +35,9 @@
 //      joining the same two slots are skipped.
 //  phase 3 (new spins §2.4 + E/M, or canonical labels)
 //    - receives the labels of the tile by one bulk copy (a run's root is
-//      the entry of its label), takes
-//      each border component's decision from its global root (its key is
-//      the cluster's canonical label, C9) and each inner component's from
-//      its own root;
+//      its label's entry), takes each border
+//      component's decision from its global root (its key is the cluster's
+//      canonical label, C9) and each inner component's from its own root;
 //    - under the flip rule (C6) the bits of a row word's 32 site indices
 //      come from one Philox block, so all inner roots of the word are
 //      decided by one draw; the flip mask of a word is built from its runs
@@ -60,6 +59,7 @@ namespace {
 constexpr int kUnionCap = 1 << 20;        // retries of one shared-memory union
 constexpr int kGlobalUnionCap = 1 << 16;  // retries of one global union
 constexpr int kGlobalFindCap = 1 << 20;   // steps of one global find
+constexpr int kListCap = 256;              // entries of a warp's work list in phase 1
 constexpr long long kBulkWaitCycles = 1LL << 31;  // ~1 s at the SM clock: limit of a bulk-copy wait
 
 // Four int8 spins (+1 = 0x01, -1 = 0xFF) -> four sign bits.
@@ -343,6 +343,17 @@ __device__ __forceinline__ RowMasks row_masks(uint32_t eB, uint32_t vB, uint32_t
   return m;
 }
 
+// Sum of v over the lanes below this one.
+__device__ __forceinline__ int warp_exclusive_sum(int v, int lane) {
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  return incl - v;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -462,16 +473,17 @@ __device__ __forceinline__ bool cta_args(const SweepArgs& a0, const BatchArgs& b
 
 // ================================================================ phase 1
 
+// Phase 1 runs one warp per 32-column band and asks for 1280 resident
+// threads an SM (at most 51 registers a thread; ten CTAs of 128 threads also
+// fit their shared memory).
 // Phase 3 runs strips of H rows; with two-row strips it asks for 1280
-// resident threads an SM (at most 51 registers a thread; ten CTAs of 128
-// threads also fit their shared memory). Taller strips would spill under that
-// bound and keep the compiler's choice.
+// resident threads an SM as well. Taller strips would spill under that bound
+// and keep the compiler's choice.
 template <int NT, int H>
 constexpr int strip_min_blocks() {
   return H == 2 ? 1280 / NT : 1;
 }
 
-// Phase 1 runs one warp per 32-column band: 1280 resident threads an SM.
 template <int NT>
 constexpr int band_min_blocks() {
   return 1280 / NT > 0 ? 1280 / NT : 1;
@@ -512,6 +524,7 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
   __shared__ int16_t s_broot[NB];
   __shared__ uint32_t s_pre[RW];  // prefix counts of s_bmask
   __shared__ uint32_t s_wsum[33];
+  __shared__ uint16_t s_list[WPR][kListCap];  // work list of each warp
   uint32_t* const s_bmask = &s_spin[0][0];  // border roots (RW words), once the bonds are drawn
 
   SweepArgs a;
@@ -661,71 +674,124 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
   }
   __syncthreads();
 
-  // ---- unions: every bond of M (the site above and the site below it carry
-  // labels of two runs that M says may differ) and every east bond across a
-  // band border. Each lane works through its own list -- the M bits of its
-  // rows, then its band border bonds -- one union per warp-wide trip.
+  // ---- unions inside the band: every bond of M (the site above and the
+  // site below it carry labels of two runs that M says may differ). The
+  // warp lists its bonds in shared memory (in rounds of kListCap) and works
+  // through the list with one state machine per lane: a lane takes the next
+  // entry as soon as its union is done, and each warp-wide trip moves every
+  // busy lane one step (both nodes a halving step up, or at two distinct roots
+  // the larger hung under the smaller). Only this warp touches its band's
+  // labels here, so a link is a plain store checked after __syncwarp: when
+  // two lanes hang the same root in one trip, one store stands and the other
+  // lane goes on from the root's new parent.
   {
-    uint32_t todo[RPL];
-    uint32_t cross = 0u;  // bit j: row lane + 32 j has an east bond into the next band
+    uint16_t* list = s_list[w];
+    int cnt = 0;
 #pragma unroll
-    for (int j = 0; j < RPL; ++j) {
-      todo[j] = mM[j];
-      const int y = lane + 32 * j;
-      if (w + 1 < WPR && y < P.nrows && (s_eint[y][w] >> 31)) cross |= 1u << j;
-    }
-    for (;;) {
-      int xa = 0, xb = 0;
-      bool have = false;
+    for (int j = 0; j < RPL; ++j) cnt += __popc(mM[j]);
+    const int first = warp_exclusive_sum(cnt, lane);
+    const int total = __shfl_sync(0xffffffffu, first + cnt, 31);
+    for (int r0 = 0; r0 < total; r0 += kListCap) {  // the same rounds in every lane
+      int idx = first;
 #pragma unroll
       for (int j = 0; j < RPL; ++j) {
-        if (!have && todo[j]) {
-          const int b = __ffs(todo[j]) - 1;
-          todo[j] &= todo[j] - 1;
-          xb = (lane + 32 * j) * TW + 32 * w + b;  // site of row lane + 32 j, bonded to the site above
+        for (uint32_t m = mM[j]; m; m &= m - 1, ++idx)
+          if (idx >= r0 && idx < r0 + kListCap)
+            list[idx - r0] = (uint16_t)((lane + 32 * j) * TW + 32 * w + __ffs(m) - 1);
+      }
+      __syncwarp();
+      const int n = min(kListCap, total - r0);
+      int k = lane, xa = 0, xb = 0;
+      bool busy = false;
+      for (int it = 0;; ++it) {
+        if (!busy && k < n) {
+          xb = list[k];  // a site bonded to the site above it
           xa = xb - TW;
-          have = true;
+          k += 32;
+          busy = true;
+        }
+        if (!__any_sync(0xffffffffu, busy)) break;
+        if (it >= kUnionCap) {
+          if (busy) atomicCAS(a.tb.err, 0, kErrUnionCap);
+          break;
+        }
+        int hi = -1, lo = 0;
+        if (busy) {
+          const int pa = par[xa], pb = par[xb];
+          if (pa == xa && pb == xb) {
+            if (xa == xb) {
+              busy = false;
+            } else {
+              hi = max(xa, xb);
+              lo = min(xa, xb);
+              par[hi] = (uint16_t)lo;
+            }
+          } else {
+            if (pa != xa) {
+              const int ga = par[pa];
+              if (ga != pa) par[xa] = (uint16_t)ga;
+              xa = ga;
+            }
+            if (pb != xb) {
+              const int gb = par[pb];
+              if (gb != pb) par[xb] = (uint16_t)gb;
+              xb = gb;
+            }
+          }
+        }
+        __syncwarp();
+        if (hi >= 0) {
+          const int now = par[hi];
+          busy = now != lo;
+          xa = now;
+          xb = lo;
         }
       }
-      if (!have && cross) {
-        const int j = __ffs(cross) - 1;
-        cross &= cross - 1;
-        xa = (lane + 32 * j) * TW + 32 * w + 31;  // last column of my word, bonded to the next word's first
-        xb = xa + 1;
-        have = true;
-      }
-      if (!__any_sync(0xffffffffu, have)) break;
-      unite_warp(par, xa, xb, have, a.tb.err);
+      __syncwarp();  // the list is rewritten by the next round
     }
   }
   __syncthreads();
 
-  // ---- every new label points at its root; roots recorded for phase 3
+  // ---- east bonds across band borders: two warps' labels, so the links are
+  // compare-and-swaps (unite_warp)
+  {
+    uint32_t cross = 0u;  // bit j: row lane + 32 j has an east bond into the next band
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+      const int y = lane + 32 * j;
+      if (w + 1 < WPR && y < P.nrows && (s_eint[y][w] >> 31)) cross |= 1u << j;
+    }
+    while (__any_sync(0xffffffffu, cross != 0u)) {
+      int xa = 0;
+      const bool have = cross != 0u;
+      if (have) {
+        xa = (lane + 32 * (__ffs(cross) - 1)) * TW + 32 * w + 31;  // last column of my word
+        cross &= cross - 1;
+      }
+      unite_warp(par, xa, xa + 1, have, a.tb.err);
+    }
+  }
+  __syncthreads();
+
+  // ---- every new label is pointed at its root, and the roots are marked
+  // for phase 3; par[par[x]] is then the root of site x. The trees are
+  // shallow: three parents are read straight away and the walk goes on only
+  // in the rare case that the third is not a root yet.
   {
     uint32_t* rb = a.tb.rbits + (size_t)P.tile * RW;
 #pragma unroll
     for (int j = 0; j < RPL; ++j) {
       const int y = lane + 32 * j, base = y * TW + 32 * w;
-      uint32_t NL = mS[j] & ~mF[j], roots = 0u;
-      // warp-wide trips (see unite_warp); a lane out of labels walks from
-      // site 0, which is always a root
-      while (__any_sync(0xffffffffu, NL != 0u)) {
-        int b = -1, r = 0;
-        if (NL) {
-          b = __ffs(NL) - 1;
-          NL &= NL - 1;
-          r = base + b;
-        }
-        int p = par[r];
-        while (__any_sync(0xffffffffu, p != r)) {
-          if (p != r) {
-            r = p;
-            p = par[r];
-          }
-        }
-        if (b >= 0) {
-          if (r == base + b) roots |= 1u << b;
-          else par[base + b] = (uint16_t)r;
+      uint32_t roots = 0u;
+      for (uint32_t m = mS[j] & ~mF[j]; m; m &= m - 1) {
+        const int b = __ffs(m) - 1, x = base + b;
+        int r = par[x];
+        if (r == x) {
+          roots |= 1u << b;
+        } else {
+          r = par[par[r]];
+          for (int p = par[r]; p != r; p = par[r]) r = p;
+          par[x] = (uint16_t)r;
         }
       }
       rb[y * WPR + w] = roots;
@@ -734,13 +800,20 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
   __syncthreads();
 
   // ---- border components -> slots (rank of the root in index order) and global nodes
-  for (int j = tid; j < NB; j += NT) {
-    int y, x, r = -1;
-    if (border_site<TW, TH>(P, j, y, x)) {
-      r = par[par[y * TW + x]];
-      atomicOr(&s_bmask[r >> 5], 1u << (r & 31));
+  for (int j0 = 0; j0 < NB; j0 += NT) {  // the same trips in every lane (a warp-wide walk)
+    const int j = j0 + tid;
+    int y = 0, x = 0, r = 0;  // a lane without a border site walks from site 0, a root
+    const bool ok = j < NB && border_site<TW, TH>(P, j, y, x);
+    if (ok) r = par[y * TW + x];
+    int p = par[r];
+    while (__any_sync(0xffffffffu, p != r)) {
+      if (p != r) {
+        r = p;
+        p = par[r];
+      }
     }
-    s_broot[j] = (int16_t)r;
+    if (ok) atomicOr(&s_bmask[r >> 5], 1u << (r & 31));
+    if (j < NB) s_broot[j] = ok ? (int16_t)r : (int16_t)-1;
   }
   __syncthreads();
   const int nsl = block_popc_prefix<RW, NT>(s_bmask, s_pre, s_wsum);
@@ -769,7 +842,7 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
     const int r = s_broot[j];
     bs[j] = r >= 0 ? (uint16_t)slot_of(s_bmask, s_pre, r) : (uint16_t)0xFFFFu;
   }
-  // labels (a root in every new label's entry) and border marks for phase 3
+  // labels and border marks for phase 3
   {
     const uint4* src = reinterpret_cast<const uint4*>(par);
     uint4* dst = reinterpret_cast<uint4*>(a.tb.roots + (size_t)P.tile * (TW * TH));
