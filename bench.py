@@ -9,9 +9,11 @@ and cross-tile cluster labelling, per-cluster flips, E/M reduction).
 
 Our arm prints one JSON line with site-updates/s measured on the device
 (CUDA events on the library's stream, L2 flushed between steps by writing a
-256 MiB buffer), the roofline of the dominant kernel, the end-to-end rate
-through the C ABI with host buffers, the oracle's CPU rate, and the SM clocks
-seen during the timed region. Under torchrun every rank runs its own replica
+256 MiB buffer; the K timed steps are repeated until they span 0.25 s and
+the median repeat is reported), the roofline of every kernel of the sweep,
+the end-to-end rate through the C ABI with host buffers, the oracle's CPU
+rates (one core on the headline lattice, every core on the 256-replica mix),
+and the SM clocks seen during the timed repeats. Under torchrun every rank runs its own replica
 (independent chains, no data-path collective: "replicas only"), and rank 0
 reports the whole-job rate.
 
@@ -46,7 +48,9 @@ BETA = 0.44068679
 SEED = 3
 N_SITES = L * L
 FLUSH_BYTES = 256 << 20
-# Tile shape of the default configuration at this L (128 x 64 sites, 2-row strips).
+MIN_CLOCK_WINDOW_S = 0.25  # timed repeats span at least this long (>= 10 clock samples)
+MAX_REPEATS = 200
+# Tile shape of the default configuration at this L (128 x 64 sites).
 TW, TH = 128, 64
 NB = 2 * TH + 2 * TW
 BBW = 2 * (TH // 32) + 2 * (TW // 32)
@@ -62,6 +66,12 @@ PHASE_BYTES_PER_TILE = {
     # bits, neighbours' halo slots in; spins out
     2: (2 * RW * 4 + 2 * TW * TH + 2 * 4 * RW + 4 + 4 * BBW + 2 * (TH + TW)) + TW * TH,
 }
+# Phase 2 + resolve touch O(tile perimeter): the tile's border bits and the
+# border slots of the tile and of its east and south neighbours, and per
+# border slot its node (read in the union walks, rewritten by the resolve
+# pass); the slot count is data dependent, so the model counts every border
+# site as a slot (an upper bound of the algorithmic bytes).
+PHASE_BYTES_PER_TILE[1] = 4 * BBW + 2 * (NB + TH + TW) + 4 + 3 * 8 * NB
 PHASE_NAMES = {0: "phase1_bonds_tile_ccl", 1: "phase2_merge_resolve", 2: "phase3_flip_em", 3: "phase4_hist"}
 SWEEP_MODEL_BYTES_PER_SITE = 10  # read spins, write+read int32 labels, write spins
 
@@ -152,6 +162,25 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- helpers
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), and its core count."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                name = line.split(":", 1)[1].strip()
+                break
+    return f"{name or 'unknown'} ({platform.machine()}, {os.cpu_count()} cores)"
+
+
 def cpu_oracle_rate(n_sweeps: int, label: str):
     """Time the serial oracle as it stands on n_sweeps of the workload."""
     import oracle
@@ -160,9 +189,44 @@ def cpu_oracle_rate(n_sweeps: int, label: str):
     t0 = time.perf_counter()
     oracle.run(L, BETA, SEED, n_sweeps, spins=s0)
     dt = time.perf_counter() - t0
-    return {"value": N_SITES * n_sweeps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": N_SITES * n_sweeps / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
             "sample": f"{n_sweeps} {label} of L={L} beta={BETA} from the oracle's own hot start "
                       f"({dt:.1f} s, serial C, {platform.machine()})"}
+
+
+def _oracle_replicas(job):
+    """One process's share of the 256-replica mix: n sweeps of each replica."""
+    import oracle
+    items, n = job
+    t0 = time.perf_counter()
+    sites = 0
+    for Lr, br, sr in items:
+        oracle.run(int(Lr), float(br), int(sr), n)
+        sites += int(Lr) * int(Lr) * n
+    return sites, time.perf_counter() - t0
+
+
+def cpu_oracle_batch_rate(n_sweeps: int):
+    """The oracle on the 256-replica mix, one process per host core (a spawn
+    pool: no process is forked from this CUDA-using one). Each process takes
+    every nproc-th replica; the rate is all site-updates over the wall time."""
+    import multiprocessing as mp
+    import oracle
+    from workloads import batch_replicas
+    oracle.build()
+    Ls, betas, seeds = batch_replicas()
+    reps = list(zip(Ls, betas, seeds))
+    order = sorted(range(len(reps)), key=lambda i: -int(reps[i][0]))   # big replicas first, dealt round robin
+    nproc = os.cpu_count() or 1
+    jobs = [([reps[i] for i in order[k::nproc]], n_sweeps) for k in range(nproc)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(nproc) as pool:
+        res = pool.map(_oracle_replicas, jobs)
+    wall = time.perf_counter() - t0
+    sites = sum(r[0] for r in res)
+    return {"value": sites / wall, "unit": UNIT, "cores": nproc, "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"{n_sweeps} oracle sweeps of each of the 256 replicas from their hot starts, "
+                      f"{nproc} processes ({wall:.1f} s wall, pool start-up included)"}
 
 
 def dist_setup(n_gpus: int):
@@ -212,18 +276,11 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    # Each step is one oracle sweep of the L = 8192 lattice; when K + W such
-    # sweeps would take longer than about 150 s on this host, each step
-    # sweeps a smaller square lattice of the same beta instead (a bounded
-    # sample; the rate is per site-update either way).
+    # Each step is one oracle sweep of the L = 8192 lattice (about 3.4 s on a
+    # Grace core), the same lattice our arm sweeps; the run takes K + W such
+    # sweeps.
     Ls = L
-    t0 = time.perf_counter()
     s, _, _, _ = oracle.run(L, BETA, SEED, 1, spins=oracle.init(L, SEED), t0=0)
-    per_sweep = time.perf_counter() - t0
-    while Ls > 512 and (args.steps + args.warmup) * per_sweep * (Ls / L) ** 2 > 150.0:
-        Ls //= 2
-    if Ls != L:
-        s = oracle.init(Ls, SEED)
     t = 1
     for _ in range(args.warmup):
         s, _, _, _ = oracle.run(Ls, BETA, SEED, 1, spins=s, t0=t)
@@ -243,10 +300,9 @@ def run_reference(args):
         "data": "synthetic (Philox hot start, seed 3)",
         "config": {"workload": f"L{L} beta_c={BETA} hot start seed {SEED}, one SW sweep per step",
                    "L": L, "beta": BETA, "seed": SEED},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
                          "sample": f"{args.steps} oracle sweeps of L={Ls} (serial C, one host core, "
-                                   f"{platform.machine()})" + ("" if Ls == L else f"; L={Ls} stands in for "
-                                   f"L={L} so that {args.steps + args.warmup} steps fit about 150 s")},
+                                   f"{platform.machine()})"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -277,19 +333,29 @@ def run_ours(args):
         lat.sweep(1)
     torch.cuda.synchronize()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # The timed region: exactly K steps, each an L2 flush and one sweep,
+    # bracketed by CUDA events on the library's stream. It is repeated until
+    # the repeats span at least MIN_CLOCK_WINDOW_S, so that the SM clock
+    # sampler (one sample per 10 ms) sees the timed work itself; `value` is
+    # the repeat with the median time, and every repeat is listed.
     t_first = lat.t
     sw.sw_timing(lat.h, True)
     barrier(world)
     torch.cuda.synchronize()
     t_region0 = time.time()
-    for k in range(args.steps):
-        flush.fill_((k + 7) & 0xFF)
-        starts[k].record(stream)
-        lat.sweep(1)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
+    repeats = []
+    while True:
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_((k + 7) & 0xFF)
+            starts[k].record(stream)
+            lat.sweep(1)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        repeats.append(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+        if time.time() - t_region0 >= MIN_CLOCK_WINDOW_S or len(repeats) >= MAX_REPEATS:
+            break
     t_region1 = time.time()
     barrier(world)
     if clocks:
@@ -297,9 +363,8 @@ def run_ours(args):
     clock_info = clocks.stop() if clocks else None
     phase_ms, phase_n = sw.sw_timing_read(lat.h)
     sw.sw_timing(lat.h, False)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    E, M = lat.observables(t_first, args.steps)
+    total_ms = sorted(repeats)[len(repeats) // 2]
+    E, M = lat.observables(t_first, args.steps * len(repeats))
     assert (np.abs(E) <= 2 * N_SITES).all() and (np.abs(M) <= N_SITES).all()
     value, max_ms = whole_job_rate(N_SITES * args.steps, total_ms, world)
 
@@ -332,6 +397,18 @@ def run_ours(args):
                              "peak_from": f"{n_sm} SMs x 4 schedulers x {mhz:.0f} MHz"}
     phases = {PHASE_NAMES[p]: {"ms_per_launch": phase_ms[p] / max(phase_n[p], 1), "launches": int(phase_n[p])}
               for p in range(4) if phase_n[p]}
+    # every kernel of the sweep against the same HBM peak: algorithmic bytes
+    # per launch (the model above) over its average CUDA-event time
+    roofline_phases = {}
+    for p in (0, 1, 2):
+        if not phase_n[p]:
+            continue
+        ms_p = phase_ms[p] / phase_n[p]
+        by = PHASE_BYTES_PER_TILE[p] * ntiles
+        gbs = by / (ms_p / 1e3) / 1e9
+        roofline_phases[PHASE_NAMES[p]] = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                                           "bytes_per_launch": by, "avg_launch_ms": ms_p,
+                                           "bytes_per_site": PHASE_BYTES_PER_TILE[p] / (TW * TH)}
     sweep_roofline_su_s = hbm_peak * 1e9 / SWEEP_MODEL_BYTES_PER_SITE
 
     # ---- end to end through the C ABI with host buffers (pinned). Two
@@ -385,16 +462,22 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(args.cpu_sweeps, "sweeps")
+        if batched is not None:
+            batched["cpu_oracle_nproc"] = cpu_oracle_batch_rate(args.cpu_batch_sweeps)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int8/u32",
         "data": "synthetic (Philox hot start, seed 3 + rank)",
         "config": {"workload": f"L{L} beta_c={BETA} hot start seed {SEED}, one SW sweep per step",
-                   "L": L, "beta": BETA, "seed": SEED, "tile": f"{TW}x{TH}, 2-row strips",
+                   "L": L, "beta": BETA, "seed": SEED, "tile": f"{TW}x{TH}, one warp per 32-column band",
                    "l2": "flushed between steps (256 MiB write), inputs 64 MiB < L2",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
+        "roofline_phases": roofline_phases,
+        "timed_repeats": {"count": len(repeats), "ms": repeats, "value_from": "median repeat",
+                          "why": "the K timed steps are repeated until they span >= 0.25 s, so the clock "
+                                 "sampler sees them"},
         "sweep_vs_10B_per_site_hbm_model": {"roofline_su_s": sweep_roofline_su_s, "frac": value / world / sweep_roofline_su_s},
         "phases": phases,
         "cpu_baseline": cpu,
@@ -616,6 +699,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=3)
+    ap.add_argument("--cpu-batch-sweeps", type=int, default=10,
+                    help="oracle sweeps of each replica in the nproc-process baseline of the 256-replica mix")
     ap.add_argument("--no-configs", action="store_true", help="skip the L=64, L=1024 and beta=0.50 lines")
     ap.add_argument("--batched-sweeps", type=int, default=500,
                     help="sweeps of the 256-replica batch (0 skips the batched and serving measurements)")

@@ -13,9 +13,10 @@ The server keeps one sw_batch. Each scheduling step it
      admitted replicas (sw_batch_footprint) stay within the memory budget,
      each with a sweep limit equal to its request (sw_batch_set_limit);
   2. advances the whole batch by one chunk of sweeps (one replay of a
-     captured CUDA graph); the chunk is the largest power of two no larger
-     than the configured chunk and the smallest remaining sweep count, so a
-     replica never idles behind a longer chunk and only a few graphs exist;
+     captured CUDA graph, the same chunk every time); a replica that
+     reaches its sweep limit inside a chunk idles for the rest of it (its
+     tiles return at once), so every request stops exactly at its count
+     while the others keep full chunks;
   3. reads back the traces of the replicas that reached their target and
      frees their slots.
 A request that cannot be served (invalid parameters, larger than the whole
@@ -103,15 +104,6 @@ class BatchBackend:
             self.b = None
 
 
-def chunk_length(chunk: int, remaining: Iterable[int]) -> int:
-    """Largest power of two <= min(chunk, every remaining count) (>= 1)."""
-    cap = min([chunk, *remaining])
-    n = 1
-    while 2 * n <= cap:
-        n *= 2
-    return n
-
-
 @dataclasses.dataclass
 class _Live:
     req: Request
@@ -197,7 +189,7 @@ class Server:
         left = {s: lv.req.sweeps - self.backend.sweep_count(s) for s, lv in self.live.items()}
         if not any(r > 0 for r in left.values()):
             return 0
-        n = chunk_length(self.chunk, [r for r in left.values() if r > 0])
+        n = self.chunk
         self.backend.sweep(n)
         for s, lv in self.live.items():
             self.site_updates += min(n, max(left[s], 0)) * lv.req.L * lv.req.L

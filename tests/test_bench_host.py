@@ -72,3 +72,21 @@ def test_clock_sampler_falls_back_to_all_samples():
     out = _sampler_from(lines, (0.0, 1.0)).stop()
     assert out["samples_in_timed_region"] == 0 and out["samples"] == 2
     assert out["sm_mhz"] == 2065.0 and out["reasons"] == []
+
+
+def test_cpu_model_names_the_host():
+    m = bench.cpu_model()
+    assert str(os.cpu_count()) in m and "cores" in m
+
+
+def test_oracle_replica_share_counts_its_site_updates():
+    # one process's share of the replica mix: n sweeps of each of its replicas
+    sites, dt = bench._oracle_replicas(([(16, 0.44, 1000), (8, 0.40, 1001)], 2))
+    assert sites == 2 * (16 * 16 + 8 * 8) and dt >= 0.0
+
+
+def test_phase_byte_models_cover_every_sweep_kernel():
+    for p in (0, 1, 2):
+        assert bench.PHASE_BYTES_PER_TILE[p] > 0
+    # phase 1 moves at least the spins in and the 16-bit labels out
+    assert bench.PHASE_BYTES_PER_TILE[0] >= 3 * bench.TW * bench.TH

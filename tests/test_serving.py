@@ -5,7 +5,7 @@ counts sweeps."""
 import pytest
 
 from paper_2302_14720_gb300 import SWError
-from paper_2302_14720_gb300.serving import Request, Server, chunk_length, latency_summary
+from paper_2302_14720_gb300.serving import Request, Server, latency_summary
 
 
 class FakeBackend:
@@ -56,12 +56,15 @@ class FakeBackend:
         pass
 
 
-def test_chunk_length_is_a_power_of_two_within_bounds():
-    assert chunk_length(64, [1000, 300]) == 64
-    assert chunk_length(64, [37, 300]) == 32
-    assert chunk_length(64, [1]) == 1
-    assert chunk_length(48, [1000]) == 32
-    assert chunk_length(1, [5]) == 1
+def test_every_chunk_has_the_configured_length():
+    # a request about to finish does not shorten the chunk of the others:
+    # its sweep limit stops it inside the chunk
+    fb = FakeBackend()
+    reqs = [Request(0, L=8, beta=0.4, seed=0, sweeps=3), Request(1, L=8, beta=0.4, seed=1, sweeps=200)]
+    with Server(budget_bytes=10 ** 9, chunk=64, backend=fb) as srv:
+        res = {r.rid: r for r in srv.run(reqs, realtime=False)}
+    assert fb.sweep_calls == [64, 64, 64, 64]
+    assert len(res[0].E) == 3 and len(res[1].E) == 200
 
 
 def test_every_request_gets_exactly_its_sweeps():
@@ -75,7 +78,7 @@ def test_every_request_gets_exactly_its_sweeps():
         n = reqs[r.rid].sweeps
         assert len(r.E) == n and list(r.E) == list(range(n))
     assert srv.site_updates == sum(q.L * q.L * q.sweeps for q in reqs)
-    assert all(n & (n - 1) == 0 and n <= 64 for n in fb.sweep_calls)
+    assert all(n == 64 for n in fb.sweep_calls)
     assert not fb.slots and srv.used == 0
 
 
