@@ -59,7 +59,6 @@ namespace {
 constexpr int kUnionCap = 1 << 20;        // retries of one shared-memory union
 constexpr int kGlobalUnionCap = 1 << 16;  // retries of one global union
 constexpr int kGlobalFindCap = 1 << 20;   // steps of one global find
-constexpr int kListCap = 256;              // entries of a warp's work list in phase 1
 constexpr long long kBulkWaitCycles = 1LL << 31;  // ~1 s at the SM clock: limit of a bulk-copy wait
 
 // Four int8 spins (+1 = 0x01, -1 = 0xFF) -> four sign bits.
@@ -517,15 +516,19 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
   constexpr int RPL = TH / 32;  // rows per lane
   static_assert(TH % 32 == 0, "whole warps of rows");
   __shared__ __align__(16) uint16_t par[TH * TW];  // label of every site; a label's entry is its union-find parent
-  __shared__ uint32_t s_spin[TH][WPR];  // the spin bits while drawing bonds, then the border-root marks
+  // spin bits and south bonds of the row words; once the row masks are
+  // built, the warps' union work lists, then the border-root marks
+  __shared__ __align__(16) uint32_t s_sd[2][TH][WPR];
   __shared__ uint32_t s_eint[TH][WPR];
-  __shared__ uint32_t s_dint[TH][WPR];
   __shared__ uint32_t s_bb[BBW];
   __shared__ int16_t s_broot[NB];
   __shared__ uint32_t s_pre[RW];  // prefix counts of s_bmask
   __shared__ uint32_t s_wsum[33];
-  __shared__ uint16_t s_list[WPR][kListCap];  // work list of each warp
-  uint32_t* const s_bmask = &s_spin[0][0];  // border roots (RW words), once the bonds are drawn
+  uint32_t(*const s_spin)[WPR] = s_sd[0];
+  uint32_t(*const s_dint)[WPR] = s_sd[1];
+  uint32_t* const s_bmask = &s_sd[0][0][0];  // border roots (RW words), after the unions
+  constexpr int kListCap = 4 * TH;           // entries of a warp's work list: fills s_sd
+  static_assert(WPR * kListCap * sizeof(uint16_t) == sizeof(s_sd), "work lists fill s_sd");
 
   SweepArgs a;
   int tile;
@@ -629,7 +632,6 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
     tb[2 * RW + rw] = d;
   }
   __syncthreads();
-  for (int i = tid; i < RW; i += NT) s_bmask[i] = 0u;  // the spin bits are no longer needed
 
   // ---- row masks of my band: warp w = word column w, lane l holds rows l + 32 j
   const int w = tid >> 5;
@@ -685,7 +687,7 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
   // two lanes hang the same root in one trip, one store stands and the other
   // lane goes on from the root's new parent.
   {
-    uint16_t* list = s_list[w];
+    uint16_t* list = reinterpret_cast<uint16_t*>(&s_sd[0][0][0]) + w * kListCap;
     int cnt = 0;
 #pragma unroll
     for (int j = 0; j < RPL; ++j) cnt += __popc(mM[j]);
@@ -751,6 +753,9 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
     }
   }
   __syncthreads();
+
+  for (int i = tid; i < RW; i += NT) s_bmask[i] = 0u;  // the work lists are done with
+  // (the next writes to s_bmask follow the barriers below)
 
   // ---- east bonds across band borders: two warps' labels, so the links are
   // compare-and-swaps (unite_warp)
@@ -961,7 +966,8 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
   __shared__ uint32_t s_wsum[33];
   __shared__ uint32_t s_flip[RW];                  // decision bit of every root (flip, or new sign)
   __shared__ uint32_t s_snew[TH][WPR];
-  __shared__ int s_slotval[MS];                    // flip bit (flip modes) or canonical label (labels mode)
+  __shared__ int s_slotkey[LABELS ? MS : 1];       // labels mode: canonical label of every slot
+  __shared__ uint32_t s_slotdec[(MS + 31) / 32];   // flip modes: decision bit of every slot
   __shared__ uint32_t s_slotroot[HIST ? MS : 1];
   __shared__ uint32_t s_hEnew[TH / 32], s_hSnew[TW / 32];
   __shared__ long long s_red[2][NT / 32];
@@ -1004,6 +1010,7 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
   }
   if (HIST)
     for (int i = tid; i < 34; i += NT) s_hist[i] = 0ull;
+  for (int i = tid; i < (MS + 31) / 32; i += NT) s_slotdec[i] = 0u;
   __syncthreads();
   const int nsl = a.tb.nslots[P.tile];
   if (block_popc_prefix<RW, NT>(s_bmask, s_pre, s_wsum) != nsl && tid == 0) atomicCAS(a.tb.err, 0, kErrSlotOverflow);
@@ -1011,7 +1018,8 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
   // ---- this tile's slots: root key and flip, as the resolve pass left them
   for (int j = tid; j < nsl; j += NT) {
     const uint64_t v = ld_node(a.tb.nodes + (uint32_t)P.tile * MS + j);
-    s_slotval[j] = LABELS ? (int)((uint32_t)(v >> 32) & 0x7fffffffu) : (int)(v >> 63);
+    if (LABELS) s_slotkey[j] = (int)((uint32_t)(v >> 32) & 0x7fffffffu);
+    else if (v >> 63) atomicOr(&s_slotdec[j >> 5], 1u << (j & 31));
     if (HIST) s_slotroot[j] = (uint32_t)v;
   }
   __syncthreads();
@@ -1047,7 +1055,7 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
         const int b = __ffs(B) - 1;
         B &= B - 1;
         const int sl = slot_of(s_bmask, s_pre, base + b);
-        fl |= (sl < nsl ? (uint32_t)s_slotval[sl] : 0u) << b;
+        fl |= (sl < nsl ? (s_slotdec[sl >> 5] >> (sl & 31)) & 1u : 0u) << b;
       }
       if (!a.rule && inner) {
         fl |= flip_bits32((uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w), a.t, a.ks) & inner;
@@ -1110,7 +1118,7 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
         int key;
         if ((s_bmask[rt >> 5] >> (rt & 31)) & 1u) {
           const int sl = slot_of(s_bmask, s_pre, rt);
-          key = sl < nsl ? s_slotval[sl] : 0;
+          key = sl < nsl ? s_slotkey[sl] : 0;
         } else {
           key = (int)((uint32_t)(P.y0 + rt / TW) * (uint32_t)L + (uint32_t)(P.x0 + rt % TW));
         }
