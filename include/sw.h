@@ -229,7 +229,8 @@ int sw_timing_read(sw_lattice* h, double* ms_out, int64_t* launches_out);
  * applies its sweep (§2) to every replica at once, each replica following
  * exactly the chain it would follow alone (same conventions C1-C10, keyed by
  * its own seed and counter), so results are bit-identical to sw_sweep.
- * Every phase of a sweep is one launch over the tiles of all replicas; an
+ * Every phase of a sweep is one launch over the tiles of all replicas, or a
+ * whole n-sweep chunk is one persistent launch (sw_batch_set_schedule); the
  * n-sweep sequence is captured as a CUDA graph and replayed while the
  * membership and n stay the same. Replicas may be added and removed between
  * sw_batch_sweep calls (continuous batching).
@@ -263,6 +264,24 @@ int sw_batch_set_limit(sw_batch* b, int32_t slot, int64_t sweeps_left);
 /* New-spin rule (SW_RULE_FLIP or SW_RULE_ASSIGN) of the replica in `slot`
  * for the sweeps that follow. */
 int sw_batch_set_rule(sw_batch* b, int32_t slot, int32_t rule);
+
+/* How sw_batch_sweep runs the sweeps (the results are the same bits either
+ * way; §2's sweep applied to every replica):
+ *   SW_SCHEDULE_PHASES (default): per sweep, one launch per phase over the
+ *     tiles of all replicas (phases 1, 2 + resolve, 3) and a counter
+ *     advance; the n-sweep sequence is one captured CUDA graph;
+ *   SW_SCHEDULE_FUSED: one persistent cooperative launch runs all n sweeps
+ *     (CTAs stay resident and take tiles in turn; the phases are separated
+ *     by grid barriers whose waits are bounded, a stuck barrier ending in
+ *     SW_ETIMEOUT from the next synchronising call), captured as a CUDA
+ *     graph with the barrier's reset (or launched directly where the
+ *     cooperative launch cannot be captured).
+ * The fused schedule needs a tile shape whose phases 1 and 3 run the same
+ * block (64-row tiles of 2-row strips, 128-row tiles of 4-row strips):
+ * SW_EINVAL otherwise. Synchronises the stream when the schedule changes. */
+#define SW_SCHEDULE_PHASES 0
+#define SW_SCHEDULE_FUSED 1
+int sw_batch_set_schedule(sw_batch* b, int32_t schedule);
 
 /* Sweep counter of the replica in `slot`. */
 int sw_batch_get_sweep(sw_batch* b, int32_t slot, uint32_t* t_out);

@@ -30,6 +30,8 @@ SW_INIT_HOT = 0
 SW_INIT_COLD = 1
 SW_RULE_FLIP = 0
 SW_RULE_ASSIGN = 1
+SW_SCHEDULE_PHASES = 0
+SW_SCHEDULE_FUSED = 1
 SW_HIST_WORDS = 34
 
 _STATUS_NAMES = {SW_EINVAL: "SW_EINVAL", SW_ENOMEM: "SW_ENOMEM", SW_ECUDA: "SW_ECUDA",
@@ -63,6 +65,7 @@ SIGNATURES = {
     "sw_batch_sweep": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sw_batch_footprint": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "sw_batch_set_rule": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "sw_batch_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sw_batch_set_limit": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
     "sw_batch_get_sweep": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32)]),
     "sw_batch_observables": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _P]),
@@ -308,6 +311,10 @@ def sw_batch_sweep(b: int, n: int) -> None:
 
 def sw_batch_set_rule(b: int, slot: int, rule: int) -> None:
     _check(_lib.sw_batch_set_rule(b, int(slot), int(rule)), "sw_batch_set_rule")
+
+
+def sw_batch_set_schedule(b: int, schedule: int) -> None:
+    _check(_lib.sw_batch_set_schedule(b, int(schedule)), "sw_batch_set_schedule")
 
 
 def sw_batch_set_limit(b: int, slot: int, sweeps_left: int) -> None:

@@ -71,8 +71,14 @@ struct sw_batch {
   bool dirty = true;        // tile map and descriptors must be rebuilt
   bool descs_stale = true;  // descriptors must be uploaded
   // Captured n-sweep graphs, one per n in use (a server runs a few chunk
-  // lengths); all are dropped when a launch width or a table moves.
+  // lengths); all are dropped when a launch width, a table or the schedule
+  // moves.
   std::vector<std::pair<int, cudaGraphExec_t>> graphs;
+  // SW_SCHEDULE_PHASES: a sweep is four launches (phases 1-3 + a counter
+  // advance); SW_SCHEDULE_FUSED: one cooperative launch runs a whole chunk.
+  int schedule = SW_SCHEDULE_PHASES;
+  sw::GridBarrier* d_gbar = nullptr;  // the fused kernel's grid barrier
+  bool fused_capture = true;          // false once capturing the cooperative launch has failed
 };
 
 namespace {
@@ -224,6 +230,7 @@ int sync_and_check_batch(sw_batch* b) {
   B_CUDA(cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag read");
   if (flag == sw::kErrUnionCap) return bfail(SW_ETIMEOUT, "device union-find retry loop reached its cap");
   if (flag == sw::kErrCopyTimeout) return bfail(SW_ETIMEOUT, "device bulk copy into shared memory did not complete");
+  if (flag == sw::kErrBarrierTimeout) return bfail(SW_ETIMEOUT, "a grid barrier of the fused batch kernel did not open");
   if (flag != 0) return bfail(SW_EDEVICE, "device error flag set");
   return SW_OK;
 }
@@ -260,6 +267,8 @@ int sw_batch_create(int32_t n, const int32_t* L, const double* beta, const uint6
   }
   if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_gbar, sizeof(sw::GridBarrier));
+  if (e == cudaSuccess) e = cudaMemset(b->d_gbar, 0, sizeof(sw::GridBarrier));
   if (e != cudaSuccess) {
     const int rc = cuda_bfail(e, "sw_batch_create");
     sw_batch_destroy(b);
@@ -351,7 +360,34 @@ int sw_batch_sweep(sw_batch* b, int32_t n) {
   int rc = sync_tables(b);
   if (rc != SW_OK) return rc;
   if (b->ntiles == 0) return SW_OK;
-  sw::BatchArgs ba{b->d_descs, b->d_tile_rep, b->desc_cap};
+  sw::BatchArgs ba{b->d_descs, b->d_tile_rep, b->desc_cap, b->d_err, b->d_gbar};
+  const bool fused = b->schedule == SW_SCHEDULE_FUSED;
+  // The n-sweep sequence: the barrier reset and one cooperative launch
+  // (fused), or per sweep the three phases and the counter advance. The
+  // fused kernel walks the whole power-of-two bucket of batch tiles (spare
+  // tiles map to no replica), like the per-phase launches.
+  auto enqueue = [&]() -> cudaError_t {
+    if (fused) {
+      cudaError_t e = cudaMemsetAsync(b->d_gbar, 0, sizeof(sw::GridBarrier), b->stream);
+      if (e == cudaSuccess) e = sw::launch_batch_fused(b->shape, ba, b->grid_tiles, n, b->stream);
+      return e;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int32_t k = 0; k < n && e == cudaSuccess; ++k) {
+      e = sw::launch_batch_phase(b->shape, 1, ba, b->grid_tiles, b->stream);
+      if (e == cudaSuccess) e = sw::launch_batch_phase(b->shape, 2, ba, b->grid_tiles, b->stream);
+      if (e == cudaSuccess) e = sw::launch_batch_phase(b->shape, 3, ba, b->grid_tiles, b->stream);
+      if (e == cudaSuccess) e = sw::launch_batch_advance(ba, b->stream);
+    }
+    return e;
+  };
+  if (fused && !b->fused_capture) {
+    // the cooperative launch could not be captured on this system: launch it
+    B_CUDA(enqueue(), "fused batch launch");
+    for (Replica& r : b->reps)
+      if (r.active) r.t += (r.t_end - r.t < n ? r.t_end - r.t : n);
+    return SW_OK;
+  }
   cudaGraphExec_t exec = nullptr;
   for (auto& g : b->graphs)
     if (g.first == n) exec = g.second;
@@ -362,17 +398,17 @@ int sw_batch_sweep(sw_batch* b, int32_t n) {
     }
     cudaGraph_t g = nullptr;
     B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
-    cudaError_t e = cudaSuccess;
-    for (int32_t k = 0; k < n && e == cudaSuccess; ++k) {
-      e = sw::launch_batch_phase(b->shape, 1, ba, b->grid_tiles, b->stream);
-      if (e == cudaSuccess) e = sw::launch_batch_phase(b->shape, 2, ba, b->grid_tiles, b->stream);
-      if (e == cudaSuccess) e = sw::launch_batch_phase(b->shape, 3, ba, b->grid_tiles, b->stream);
-      if (e == cudaSuccess) e = sw::launch_batch_advance(ba, b->stream);
-    }
+    cudaError_t e = enqueue();
     const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
     if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess && fused) {
+      // capture of the cooperative launch refused: launch it directly from now on
+      cudaGetLastError();
+      b->fused_capture = false;
+      return sw_batch_sweep(b, n);
+    }
     if (e != cudaSuccess) return cuda_bfail(e, "graph capture of the batch sweep");
     b->graphs.emplace_back(n, exec);
   }
@@ -388,6 +424,20 @@ int sw_batch_set_limit(sw_batch* b, int32_t slot, int64_t sweeps_left) {
   Replica& r = b->reps[slot];
   r.t_end = sweeps_left < 0 ? INT64_MAX : r.t + sweeps_left;
   b->descs_stale = true;
+  return SW_OK;
+}
+
+int sw_batch_set_schedule(sw_batch* b, int32_t schedule) {
+  if (!b) return bfail(SW_EINVAL, "batch is NULL");
+  if (schedule != SW_SCHEDULE_PHASES && schedule != SW_SCHEDULE_FUSED)
+    return bfail(SW_EINVAL, "schedule must be SW_SCHEDULE_PHASES or SW_SCHEDULE_FUSED");
+  if (schedule == SW_SCHEDULE_FUSED && !sw::batch_fused_supported(b->shape))
+    return bfail(SW_EINVAL, "the fused schedule needs a tile shape whose phases 1 and 3 take the same block");
+  if (schedule != b->schedule) {
+    B_CUDA(cudaStreamSynchronize(b->stream), "stream synchronize");
+    drop_graph(b);
+    b->schedule = schedule;
+  }
   return SW_OK;
 }
 
@@ -473,6 +523,7 @@ int sw_batch_destroy(sw_batch* b) {
   if (b->d_descs) cudaFree(b->d_descs);
   if (b->d_tile_rep) cudaFree(b->d_tile_rep);
   if (b->d_err) cudaFree(b->d_err);
+  if (b->d_gbar) cudaFree(b->d_gbar);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return SW_OK;

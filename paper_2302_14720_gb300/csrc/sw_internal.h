@@ -15,9 +15,11 @@ enum DeviceError : int {
   kErrBadSpin = 2,      // sw_set_state from device memory saw a value other than +1/-1
   kErrSlotOverflow = 3, // more boundary components than slots (cannot happen; checked)
   kErrCopyTimeout = 4,  // a bulk copy into shared memory did not land within its time limit
+  kErrBarrierTimeout = 5,  // a grid barrier of the fused batch kernel did not open within its time limit
 };
 
-// A tile shape: TW = 32*WPR columns by TH rows. Each thread owns one 32-site
+// A tile shape: TW = 32*WPR columns by TH rows. Phase 1 runs one warp per
+// 32-column band (32 * WPR threads); in phase 3 each thread owns one 32-site
 // word column of an H-row strip of the tile (WPR * TH/H threads per tile).
 // Tiles are laid over the L x L lattice from the origin; the last tile
 // column and row may be ragged.
@@ -53,7 +55,7 @@ __host__ __device__ constexpr TileShape shape_of(int v) {
 // Per-lattice device buffers of the tile pipeline.
 struct TileBuffers {
   uint32_t* tbits;   // [ntiles][3][row_words]: spin bits, east-bond bits, south-bond bits per row-word
-  uint16_t* roots;   // [ntiles][sites]: tile-local root of every run start (phase 1 -> phase 3)
+  uint16_t* roots;   // [ntiles][sites]: tile-local label of every site; a label's entry is its root (phase 1 -> phase 3)
   uint32_t* bmask;   // [ntiles][row_words]: bit set at every tile root that touches the tile border
   uint32_t* rbits;   // [ntiles][row_words]: bit set at every tile root
   uint64_t* nodes;   // [ntiles * max_slots]: global union-find, (key << 32) | parent node
@@ -100,10 +102,18 @@ struct ReplicaDesc {
   int64_t em_next;    // trace row of the next sweep
 };
 
+// Arrival count and generation of the fused batch kernel's grid barrier.
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
 struct BatchArgs {
   ReplicaDesc* descs;
   const int* tile_rep;  // batch tile -> replica index
   int nrep;
+  int* err;             // the batch's device error flag (fused kernel)
+  GridBarrier* gbar;    // the fused kernel's grid barrier (zeroed before each launch)
 };
 
 // Set the thread's last error message (sw_last_error) and return code.
@@ -128,6 +138,12 @@ cudaError_t launch_phase4(int shape, const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_batch_phase(int shape, int which, const BatchArgs& b, int ntiles, cudaStream_t st);
 // Batch: advance every active replica's sweep counter and trace row by one.
 cudaError_t launch_batch_advance(const BatchArgs& b, cudaStream_t st);
+// Batch, fused schedule: one cooperative launch runs nsweeps whole sweeps of
+// every replica with tiles (all four phases, grid barriers between them) and
+// advances the replicas' counters itself. Only shapes whose phases 1 and 3
+// take the same block (TH == 32 H) have it: batch_fused_supported.
+bool batch_fused_supported(int shape);
+cudaError_t launch_batch_fused(int shape, const BatchArgs& b, int ntiles, int nsweeps, cudaStream_t st);
 
 // Whole sweeps of one small lattice in one CTA (sw_small.cu). 181^2 < 2^15,
 // so 16-bit parents index every site.

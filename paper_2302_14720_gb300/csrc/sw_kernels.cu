@@ -71,16 +71,18 @@ __device__ __forceinline__ uint32_t spin_bytes4(uint32_t nib) {
   return 0x01010101u | (spread * 0xFEu);
 }
 
+// Spins are loaded past L1 (ld.cg): other CTAs of the fused batch kernel
+// write them earlier in the same launch, and L1 is not kept coherent.
 __device__ __forceinline__ uint32_t load_spin_bits(const int8_t* p, int nb, bool vec) {
   if (vec && nb == 32) {
     const uint4* q = reinterpret_cast<const uint4*>(p);
-    const uint4 u = __ldg(q), v = __ldg(q + 1);
+    const uint4 u = __ldcg(q), v = __ldcg(q + 1);
     return sign_bits4(u.x) | (sign_bits4(u.y) << 4) | (sign_bits4(u.z) << 8) | (sign_bits4(u.w) << 12) |
            (sign_bits4(v.x) << 16) | (sign_bits4(v.y) << 20) | (sign_bits4(v.z) << 24) |
            (sign_bits4(v.w) << 28);
   }
   uint32_t bits = 0;
-  for (int k = 0; k < nb; ++k) bits |= (uint32_t)(p[k] < 0) << k;
+  for (int k = 0; k < nb; ++k) bits |= (uint32_t)(__ldcg(p + k) < 0) << k;
   return bits;
 }
 
@@ -452,22 +454,26 @@ __device__ __forceinline__ int slot_of(const uint32_t* bmask, const uint32_t* pr
 
 // The sweep arguments of this CTA's tile: the kernel parameter for one
 // lattice, or the replica descriptor of the batch tile blockIdx.x.
+// The sweep arguments of a tile: the kernel parameter for one lattice (tile
+// T), or the replica descriptor of batch tile T. k: sweeps past the
+// descriptor's counter (the fused batch kernel runs several sweeps in one
+// launch; a replica takes part in sweep k only while k < its sweeps left).
 template <bool BATCH>
-__device__ __forceinline__ bool cta_args(const SweepArgs& a0, const BatchArgs& b, SweepArgs& A, int& tile) {
+__device__ __forceinline__ bool cta_args(const SweepArgs& a0, const BatchArgs& b, int T, int k, SweepArgs& A,
+                                         int& tile) {
   if (!BATCH) {
     A = a0;
-    tile = blockIdx.x;
+    tile = T;
     return true;
   }
-  const int T = blockIdx.x;
   const int r = b.tile_rep[T];
   if (r < 0) return false;  // a spare tile of the launch bucket
   const ReplicaDesc* D = b.descs + r;
   A = D->a;
-  A.t = D->t;
-  A.em = D->em_base + 2 * D->em_next;
+  A.t = D->t + (uint32_t)k;
+  A.em = D->em_base + 2 * (D->em_next + k);
   tile = T - D->tile0;
-  return D->active != 0 && D->t_left > 0;
+  return D->active != 0 && D->t_left > k;
 }
 
 // ================================================================ phase 1
@@ -507,23 +513,36 @@ constexpr int band_min_blocks() {
 //     "lowest value label" of §2.3;
 //  5. border components get slots and global nodes, as the cross-tile merge
 //     (phase 2) needs them; par, the masks and the tables go to global memory.
-template <int WPR, int TH, int H, bool BATCH>
-__global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
-    phase1_kernel(const SweepArgs a0, const BatchArgs bat) {
+// Shared memory of phase 1 for one tile.
+template <int WPR, int TH, int H>
+struct P1Shared {
   using T = Tile<WPR, TH, H>;
-  constexpr int TW = T::TW, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
+  alignas(16) uint16_t par[TH * T::TW];  // label of every site; a label's entry is its union-find parent
+  // spin bits and south bonds of the row words; once the row masks are
+  // built, the warps' union work lists, then the border-root marks
+  alignas(16) uint32_t sd[2][TH][WPR];
+  uint32_t eint[TH][WPR];
+  uint32_t bb[T::BBW];
+  int16_t broot[T::NB];
+  uint32_t pre[T::RW];  // prefix counts of the border-root marks
+  uint32_t wsum[33];
+};
+
+template <int WPR, int TH, int H, bool BATCH>
+__device__ __forceinline__ void phase1_body(P1Shared<WPR, TH, H>& S, const SweepArgs& a0, const BatchArgs& bat,
+                                            int T, int k) {
+  using Tl = Tile<WPR, TH, H>;
+  constexpr int TW = Tl::TW, NB = Tl::NB, MS = Tl::MS, BBW = Tl::BBW, RW = Tl::RW;
   constexpr int NT = 32 * WPR;  // threads of phase 1
   constexpr int RPL = TH / 32;  // rows per lane
   static_assert(TH % 32 == 0, "whole warps of rows");
-  __shared__ __align__(16) uint16_t par[TH * TW];  // label of every site; a label's entry is its union-find parent
-  // spin bits and south bonds of the row words; once the row masks are
-  // built, the warps' union work lists, then the border-root marks
-  __shared__ __align__(16) uint32_t s_sd[2][TH][WPR];
-  __shared__ uint32_t s_eint[TH][WPR];
-  __shared__ uint32_t s_bb[BBW];
-  __shared__ int16_t s_broot[NB];
-  __shared__ uint32_t s_pre[RW];  // prefix counts of s_bmask
-  __shared__ uint32_t s_wsum[33];
+  uint16_t* const par = S.par;
+  uint32_t(&s_sd)[2][TH][WPR] = S.sd;
+  uint32_t(&s_eint)[TH][WPR] = S.eint;
+  uint32_t* const s_bb = S.bb;
+  int16_t* const s_broot = S.broot;
+  uint32_t* const s_pre = S.pre;
+  uint32_t* const s_wsum = S.wsum;
   uint32_t(*const s_spin)[WPR] = s_sd[0];
   uint32_t(*const s_dint)[WPR] = s_sd[1];
   uint32_t* const s_bmask = &s_sd[0][0][0];  // border roots (RW words), after the unions
@@ -532,15 +551,15 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
 
   SweepArgs a;
   int tile;
-  if (!cta_args<BATCH>(a0, bat, a, tile)) return;
+  if (!cta_args<BATCH>(a0, bat, T, k, a, tile)) return;
   const Geometry& g = a.g;
   const int L = g.L;
   const TilePos P = tile_pos<TW, TH>(g, tile);
   const int tid = threadIdx.x, lane = tid & 31, warp0 = tid & ~31;
-  uint32_t* eout = s_bb + T::OFF_EOUT;
-  uint32_t* sout = s_bb + T::OFF_SOUT;
-  uint32_t* hE = s_bb + T::OFF_HE;
-  uint32_t* hS = s_bb + T::OFF_HS;
+  uint32_t* eout = s_bb + Tl::OFF_EOUT;
+  uint32_t* sout = s_bb + Tl::OFF_SOUT;
+  uint32_t* hE = s_bb + Tl::OFF_HE;
+  uint32_t* hS = s_bb + Tl::OFF_HS;
 
   for (int i = tid; i < BBW; i += NT) s_bb[i] = 0u;
 
@@ -561,7 +580,7 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
   const int ys = (P.y0 + P.nrows) % L;
   for (int b0 = warp0; b0 < TH; b0 += NT) {
     const int y = b0 + lane;
-    const bool bit = y < P.nrows && a.spins_in[(size_t)(P.y0 + y) * L + xe] < 0;
+    const bool bit = y < P.nrows && __ldcg(a.spins_in + (size_t)(P.y0 + y) * L + xe) < 0;
     const uint32_t m = __ballot_sync(0xffffffffu, bit);
     if (lane == 0) hE[b0 >> 5] = m;
   }
@@ -866,53 +885,68 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
   }
 }
 
+template <int WPR, int TH, int H, bool BATCH>
+__global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
+    phase1_kernel(const SweepArgs a0, const BatchArgs bat) {
+  __shared__ P1Shared<WPR, TH, H> S;
+  phase1_body<WPR, TH, H, BATCH>(S, a0, bat, blockIdx.x, 0);
+}
+
 // ================================================================ phase 2
 
-// One CTA per tile, one thread per out-going border edge: TH east edges (rows)
-// then TW south edges (columns).
+// Per tile, every out-going border edge: TH east edges (rows) then TW south
+// edges (columns), one edge per thread at a time.
 template <int WPR, int TH, int H, bool BATCH>
-__global__ void phase2_kernel(const SweepArgs a0, const BatchArgs bat) {
-  using T = Tile<WPR, TH, H>;
-  constexpr int TW = T::TW, NB = T::NB, MS = T::MS, BBW = T::BBW;
+__device__ __forceinline__ void phase2_body(const SweepArgs& a0, const BatchArgs& bat, int T, int k) {
+  using Tl = Tile<WPR, TH, H>;
+  constexpr int TW = Tl::TW, NB = Tl::NB, MS = Tl::MS, BBW = Tl::BBW;
   SweepArgs a;
   int tile;
-  if (!cta_args<BATCH>(a0, bat, a, tile)) return;
+  if (!cta_args<BATCH>(a0, bat, T, k, a, tile)) return;
   const Geometry& g = a.g;
-  const int k = threadIdx.x;
   const TilePos P = tile_pos<TW, TH>(g, tile);
   const uint32_t* bb = a.tb.bbits + (size_t)tile * BBW;
   const uint16_t* bs = a.tb.bslot + (size_t)tile * NB;
-  if (k < TH) {
-    const int y = k;
-    if (y >= P.nrows) return;
-    const uint32_t* eo = bb + T::OFF_EOUT;
-    if (!((eo[y >> 5] >> (y & 31)) & 1u)) return;
-    const int tileE = P.ty * g.tiles_x + (P.tx + 1) % g.tiles_x;
-    const uint16_t* bsE = a.tb.bslot + (size_t)tileE * NB;
-    const uint16_t sa = bs[TH + y], sb = bsE[y];
-    if (sa >= a.tb.nslots[tile] || sb >= a.tb.nslots[tileE]) {
-      atomicCAS(a.tb.err, 0, kErrSlotOverflow);
-      return;
+  for (int e = threadIdx.x; e < TH + TW; e += blockDim.x) {
+    if (e < TH) {
+      const int y = e;
+      if (y >= P.nrows) continue;
+      const uint32_t* eo = bb + Tl::OFF_EOUT;
+      if (!((eo[y >> 5] >> (y & 31)) & 1u)) continue;
+      const int tileE = P.ty * g.tiles_x + (P.tx + 1) % g.tiles_x;
+      const uint16_t* bsE = a.tb.bslot + (size_t)tileE * NB;
+      const uint16_t sa = __ldcg(bs + TH + y), sb = __ldcg(bsE + y);
+      if (sa >= __ldcg(a.tb.nslots + tile) || sb >= __ldcg(a.tb.nslots + tileE)) {
+        atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+        continue;
+      }
+      if (y > 0 && ((eo[(y - 1) >> 5] >> ((y - 1) & 31)) & 1u) && __ldcg(bs + TH + y - 1) == sa &&
+          __ldcg(bsE + y - 1) == sb)
+        continue;
+      unite_global(a.tb.nodes, (uint32_t)tile * MS + sa, (uint32_t)tileE * MS + sb, a.tb.err);
+    } else {
+      const int x = e - TH;
+      if (x >= P.ncols) continue;
+      const uint32_t* so = bb + Tl::OFF_SOUT;
+      if (!((so[x >> 5] >> (x & 31)) & 1u)) continue;
+      const int tileS = ((P.ty + 1) % g.tiles_y) * g.tiles_x + P.tx;
+      const uint16_t* bsS = a.tb.bslot + (size_t)tileS * NB;
+      const uint16_t sa = __ldcg(bs + 2 * TH + TW + x), sb = __ldcg(bsS + 2 * TH + x);
+      if (sa >= __ldcg(a.tb.nslots + tile) || sb >= __ldcg(a.tb.nslots + tileS)) {
+        atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+        continue;
+      }
+      if (x > 0 && ((so[(x - 1) >> 5] >> ((x - 1) & 31)) & 1u) && __ldcg(bs + 2 * TH + TW + x - 1) == sa &&
+          __ldcg(bsS + 2 * TH + x - 1) == sb)
+        continue;
+      unite_global(a.tb.nodes, (uint32_t)tile * MS + sa, (uint32_t)tileS * MS + sb, a.tb.err);
     }
-    if (y > 0 && ((eo[(y - 1) >> 5] >> ((y - 1) & 31)) & 1u) && bs[TH + y - 1] == sa && bsE[y - 1] == sb) return;
-    unite_global(a.tb.nodes, (uint32_t)tile * MS + sa, (uint32_t)tileE * MS + sb, a.tb.err);
-  } else if (k < TH + TW) {
-    const int x = k - TH;
-    if (x >= P.ncols) return;
-    const uint32_t* so = bb + T::OFF_SOUT;
-    if (!((so[x >> 5] >> (x & 31)) & 1u)) return;
-    const int tileS = ((P.ty + 1) % g.tiles_y) * g.tiles_x + P.tx;
-    const uint16_t* bsS = a.tb.bslot + (size_t)tileS * NB;
-    const uint16_t sa = bs[2 * TH + TW + x], sb = bsS[2 * TH + x];
-    if (sa >= a.tb.nslots[tile] || sb >= a.tb.nslots[tileS]) {
-      atomicCAS(a.tb.err, 0, kErrSlotOverflow);
-      return;
-    }
-    if (x > 0 && ((so[(x - 1) >> 5] >> ((x - 1) & 31)) & 1u) && bs[2 * TH + TW + x - 1] == sa &&
-        bsS[2 * TH + x - 1] == sb)
-      return;
-    unite_global(a.tb.nodes, (uint32_t)tile * MS + sa, (uint32_t)tileS * MS + sb, a.tb.err);
   }
+}
+
+template <int WPR, int TH, int H, bool BATCH>
+__global__ void phase2_kernel(const SweepArgs a0, const BatchArgs bat) {
+  phase2_body<WPR, TH, H, BATCH>(a0, bat, blockIdx.x, 0);
 }
 
 // ------------------------------------------------------------- resolve
@@ -927,11 +961,11 @@ __global__ void phase2_kernel(const SweepArgs a0, const BatchArgs bat) {
 // ancestor, so walks of other threads that meet a rewritten node still end
 // at the same root. Phase 3 then reads a slot's decision in one load.
 template <int WPR, int TH, int H, bool BATCH>
-__global__ void resolve_kernel(const SweepArgs a0, const BatchArgs bat) {
+__device__ __forceinline__ void resolve_body(const SweepArgs& a0, const BatchArgs& bat, int T, int k) {
   constexpr int MS = Tile<WPR, TH, H>::MS;
   SweepArgs a;
   int tile;
-  if (!cta_args<BATCH>(a0, bat, a, tile)) return;
+  if (!cta_args<BATCH>(a0, bat, T, k, a, tile)) return;
   const int nsl = min(a.tb.nslots[tile], MS);
   for (int j = threadIdx.x; j < nsl; j += blockDim.x) {
     const uint32_t x = (uint32_t)tile * MS + j;
@@ -951,33 +985,60 @@ __global__ void resolve_kernel(const SweepArgs a0, const BatchArgs bat) {
   }
 }
 
+template <int WPR, int TH, int H, bool BATCH>
+__global__ void resolve_kernel(const SweepArgs a0, const BatchArgs bat) {
+  resolve_body<WPR, TH, H, BATCH>(a0, bat, blockIdx.x, 0);
+}
+
 // ================================================================ phase 3
 
 // MODE 0: flips + E/M; 1: flips + E/M + cluster sizes; 2: canonical labels.
-template <int WPR, int TH, int H, int MODE, bool BATCH>
-__global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H), H>())
-    phase3_kernel(const SweepArgs a0, const BatchArgs bat) {
+// Shared memory of phase 3 for one tile.
+template <int WPR, int TH, int H, int MODE>
+struct P3Shared {
   using T = Tile<WPR, TH, H>;
-  constexpr int TW = T::TW, NT = T::NT, NB = T::NB, MS = T::MS, BBW = T::BBW, RW = T::RW;
+  static constexpr bool HIST = MODE == 1, LABELS = MODE == 2;
+  alignas(16) uint16_t par[TH * T::TW];  // labels from phase 1: par[par[x]] is the tile root of x
+  uint32_t bmask[T::RW];                 // border roots
+  uint32_t pre[T::RW];
+  uint32_t wsum[33];
+  uint32_t flip[T::RW];                  // decision bit of every root (flip, or new sign)
+  uint32_t snew[TH][WPR];
+  int slotkey[LABELS ? T::MS : 1];       // labels mode: canonical label of every slot
+  uint32_t slotdec[(T::MS + 31) / 32];   // flip modes: decision bit of every slot
+  uint32_t slotroot[HIST ? T::MS : 1];
+  uint32_t hEnew[TH / 32], hSnew[T::TW / 32];
+  long long red[2][T::NT / 32];
+  unsigned long long hist[HIST ? 34 : 1];
+  unsigned long long roots_bar;          // completion of the labels tile's bulk copy into par
+};
+
+// Returns false when the labels' bulk copy did not land (the CTA's shared
+// memory may still be written by it: the caller must not reuse it).
+template <int WPR, int TH, int H, int MODE, bool BATCH>
+__device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, int* s_size, const SweepArgs& a0,
+                                            const BatchArgs& bat, int T, int ksweep) {
+  using Tl = Tile<WPR, TH, H>;
+  constexpr int TW = Tl::TW, NT = Tl::NT, NB = Tl::NB, MS = Tl::MS, BBW = Tl::BBW, RW = Tl::RW;
   constexpr bool HIST = MODE == 1, LABELS = MODE == 2;
-  __shared__ __align__(16) uint16_t par[TH * TW];  // labels from phase 1: par[par[x]] is the tile root of x
-  __shared__ uint32_t s_bmask[RW];                 // border roots
-  __shared__ uint32_t s_pre[RW];
-  __shared__ uint32_t s_wsum[33];
-  __shared__ uint32_t s_flip[RW];                  // decision bit of every root (flip, or new sign)
-  __shared__ uint32_t s_snew[TH][WPR];
-  __shared__ int s_slotkey[LABELS ? MS : 1];       // labels mode: canonical label of every slot
-  __shared__ uint32_t s_slotdec[(MS + 31) / 32];   // flip modes: decision bit of every slot
-  __shared__ uint32_t s_slotroot[HIST ? MS : 1];
-  __shared__ uint32_t s_hEnew[TH / 32], s_hSnew[TW / 32];
-  __shared__ long long s_red[2][NT / 32];
-  __shared__ unsigned long long s_hist[HIST ? 34 : 1];
-  __shared__ unsigned long long s_roots_bar;       // completion of the roots tile's bulk copy into par
-  extern __shared__ __align__(16) int s_size[];  // HIST: [TH * TW]
+  uint16_t* const par = S.par;
+  uint32_t* const s_bmask = S.bmask;
+  uint32_t* const s_pre = S.pre;
+  uint32_t* const s_wsum = S.wsum;
+  uint32_t* const s_flip = S.flip;
+  uint32_t(&s_snew)[TH][WPR] = S.snew;
+  int* const s_slotkey = S.slotkey;
+  uint32_t* const s_slotdec = S.slotdec;
+  uint32_t* const s_slotroot = S.slotroot;
+  uint32_t* const s_hEnew = S.hEnew;
+  uint32_t* const s_hSnew = S.hSnew;
+  long long(&s_red)[2][NT / 32] = S.red;
+  unsigned long long* const s_hist = S.hist;
+  unsigned long long& s_roots_bar = S.roots_bar;
 
   SweepArgs a;
   int tile;
-  if (!cta_args<BATCH>(a0, bat, a, tile)) return;
+  if (!cta_args<BATCH>(a0, bat, T, ksweep, a, tile)) return true;
   const Geometry& g = a.g;
   const int L = g.L;
   const TilePos P = tile_pos<TW, TH>(g, tile);
@@ -1096,8 +1157,11 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
     if (!landed) atomicCAS(a.tb.err, 0, kErrCopyTimeout);
     if (__syncthreads_or(!landed)) {
       if (!landed) bulk_load_wait(&s_roots_bar);  // once more before the CTA's shared memory is released
-      return;
+      return false;
     }
+    // every thread has passed the wait: the barrier's word may be reused
+    // (the fused batch kernel overlays it with other data)
+    if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&s_roots_bar)) : "memory");
   }
 
   // ---- per run: its root's decision; new spins of my strip
@@ -1145,7 +1209,7 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
       store_spin_bits(a.spins_out + (size_t)(P.y0 + y) * L + P.x0 + 32 * w, snew[r], nb, g.aligned16);
     }
   }
-  if (LABELS) return;
+  if (LABELS) return true;
 #pragma unroll
   for (int r = 0; r < H; ++r) s_snew[y0r + r][w] = snew[r];
 
@@ -1156,13 +1220,13 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
     bool bit = false;
     if (y < P.nrows) {
       const int tileE = P.ty * g.tiles_x + (P.tx + 1) % g.tiles_x;
-      uint16_t slot = a.tb.bslot[(size_t)tileE * NB + y];
+      uint16_t slot = __ldcg(a.tb.bslot + (size_t)tileE * NB + y);
       if (slot >= MS) {
         atomicCAS(a.tb.err, 0, kErrSlotOverflow);
         slot = 0;
       }
       const uint64_t v = ld_node(a.tb.nodes + (uint32_t)tileE * MS + slot);
-      const uint32_t old = (bbits[T::OFF_HE + (y >> 5)] >> (y & 31)) & 1u;
+      const uint32_t old = (bbits[Tl::OFF_HE + (y >> 5)] >> (y & 31)) & 1u;
       bit = ((a.rule ? 0u : old) ^ (uint32_t)(v >> 63)) != 0u;
     }
     const uint32_t m = __ballot_sync(0xffffffffu, bit);
@@ -1173,13 +1237,13 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
     bool bit = false;
     if (x < P.ncols) {
       const int tileS = ((P.ty + 1) % g.tiles_y) * g.tiles_x + P.tx;
-      uint16_t slot = a.tb.bslot[(size_t)tileS * NB + 2 * TH + x];
+      uint16_t slot = __ldcg(a.tb.bslot + (size_t)tileS * NB + 2 * TH + x);
       if (slot >= MS) {
         atomicCAS(a.tb.err, 0, kErrSlotOverflow);
         slot = 0;
       }
       const uint64_t v = ld_node(a.tb.nodes + (uint32_t)tileS * MS + slot);
-      const uint32_t old = (bbits[T::OFF_HS + (x >> 5)] >> (x & 31)) & 1u;
+      const uint32_t old = (bbits[Tl::OFF_HS + (x >> 5)] >> (x & 31)) & 1u;
       bit = ((a.rule ? 0u : old) ^ (uint32_t)(v >> 63)) != 0u;
     }
     const uint32_t m = __ballot_sync(0xffffffffu, bit);
@@ -1255,6 +1319,15 @@ __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H
   if (HIST)
     for (int i = tid; i < 34; i += NT)
       if (s_hist[i]) atomicAdd(reinterpret_cast<unsigned long long*>(a.hist + i), s_hist[i]);
+  return true;
+}
+
+template <int WPR, int TH, int H, int MODE, bool BATCH>
+__global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H), H>())
+    phase3_kernel(const SweepArgs a0, const BatchArgs bat) {
+  __shared__ P3Shared<WPR, TH, H, MODE> S;
+  extern __shared__ __align__(16) int s_size[];  // HIST: [TH * TW]
+  phase3_body<WPR, TH, H, MODE, BATCH>(S, s_size, a0, bat, blockIdx.x, 0);
 }
 
 // ================================================================ phase 4
@@ -1295,6 +1368,121 @@ __global__ void batch_advance_kernel(const BatchArgs b) {
   D->t += 1;
   D->em_next += 1;
   D->t_left -= 1;
+}
+
+// ========================================================== fused batch kernel
+
+constexpr long long kBarrierWaitCycles = 1LL << 31;  // ~1 s at the SM clock: limit of a grid-barrier wait
+
+// Grid-wide barrier of the fused batch kernel. Every thread fences its
+// global writes, then one thread per CTA arrives (an atomic add on the
+// count); the last to arrive resets the count and opens the next
+// generation, the others wait for it. Every CTA of the launch must be
+// resident, which the cooperative launch guarantees (or it fails). The wait
+// is bounded (about a second): then the CTA raises kErrBarrierTimeout and
+// the function returns false, and the caller returns.
+__device__ bool grid_sync(GridBarrier* gb, int* err) {
+  __shared__ int s_ok;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* vgen = &gb->gen;
+    const unsigned int gen = *vgen;
+    __threadfence();
+    if (atomicAdd(&gb->count, 1u) + 1u == gridDim.x) {
+      gb->count = 0u;
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > kBarrierWaitCycles) {
+          atomicCAS(err, 0, kErrBarrierTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int WPR, int TH, int H>
+union FusedShared {
+  P1Shared<WPR, TH, H> p1;
+  P3Shared<WPR, TH, H, 0> p3;
+};
+
+// nsweeps whole sweeps of every replica with tiles, in one launch: the
+// phases of a sweep run over all batch tiles (CTA c takes tiles c, c + grid,
+// ...), separated by grid barriers, since a phase reads what the previous
+// one wrote for neighbouring tiles. Replica r takes part in sweep k while
+// k < its sweeps left (cta_args). At the end CTA 0 advances every replica's
+// counter and trace row by the sweeps it ran. The phases are the same code
+// as the separate launches (the *_body functions), so the results are too.
+template <int WPR, int TH, int H>
+__global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
+    batch_fused_kernel(const BatchArgs b, int nsweeps, int ntiles) {
+  static_assert(Tile<WPR, TH, H>::NT == 32 * WPR, "phases 1 and 3 run the same block");
+  __shared__ FusedShared<WPR, TH, H> U;
+  const SweepArgs none{};
+  for (int k = 0; k < nsweeps; ++k) {
+    for (int T = blockIdx.x; T < ntiles; T += gridDim.x) {
+      phase1_body<WPR, TH, H, true>(U.p1, none, b, T, k);
+      __syncthreads();  // the next tile reuses the shared memory
+    }
+    if (!grid_sync(b.gbar, b.err)) return;
+    for (int T = blockIdx.x; T < ntiles; T += gridDim.x) phase2_body<WPR, TH, H, true>(none, b, T, k);
+    if (!grid_sync(b.gbar, b.err)) return;
+    for (int T = blockIdx.x; T < ntiles; T += gridDim.x) resolve_body<WPR, TH, H, true>(none, b, T, k);
+    if (!grid_sync(b.gbar, b.err)) return;
+    for (int T = blockIdx.x; T < ntiles; T += gridDim.x) {
+      const bool ok = phase3_body<WPR, TH, H, 0, true>(U.p3, nullptr, none, b, T, k);
+      __syncthreads();
+      if (!ok) return;  // a bulk copy may still write this CTA's shared memory
+    }
+    if (!grid_sync(b.gbar, b.err)) return;
+  }
+  if (blockIdx.x == 0) {
+    for (int r = threadIdx.x; r < b.nrep; r += blockDim.x) {
+      ReplicaDesc* D = b.descs + r;
+      if (!D->active || D->t_left <= 0) continue;
+      const int64_t m = D->t_left < nsweeps ? D->t_left : nsweeps;
+      D->t += (uint32_t)m;
+      D->em_next += m;
+      D->t_left -= m;
+    }
+  }
+}
+
+template <int WPR, int TH, int H>
+cudaError_t launch_fused_shape(const BatchArgs& b, int ntiles, int nsweeps, cudaStream_t st) {
+  auto kern = batch_fused_kernel<WPR, TH, H>;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * WPR, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  int grid = per_sm * nsm;
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(32 * WPR);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, b, nsweeps, ntiles);
 }
 
 // ================================================================ helpers
@@ -1454,6 +1642,21 @@ cudaError_t launch_batch_advance(const BatchArgs& b, cudaStream_t st) {
   if (b.nrep <= 0) return cudaSuccess;
   batch_advance_kernel<<<(b.nrep + 127) / 128, 128, 0, st>>>(b);
   return cudaGetLastError();
+}
+
+bool batch_fused_supported(int shape) {
+  if (shape < 0 || shape >= kNumShapes) return false;
+  const TileShape ts = shape_of(shape);
+  return ts.th == 32 * ts.h;
+}
+
+cudaError_t launch_batch_fused(int shape, const BatchArgs& b, int ntiles, int nsweeps, cudaStream_t st) {
+  if (ntiles <= 0 || nsweeps <= 0) return cudaSuccess;
+  switch (shape) {
+    case 4: return launch_fused_shape<shape_of(4).wpr, shape_of(4).th, shape_of(4).h>(b, ntiles, nsweeps, st);
+    case 6: return launch_fused_shape<shape_of(6).wpr, shape_of(6).th, shape_of(6).h>(b, ntiles, nsweeps, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace sw

@@ -146,3 +146,88 @@ def test_autotune_installs_a_measured_shape(sw):
         want_s, want_E, _, _ = oracle.run(300, 0.44, 5, 3)
         assert np.array_equal(lat.spins(), want_s)
     sw.sw_tune_shape(b, -1)
+
+
+# ------------------------------------------------- fused schedule (one launch per chunk)
+
+@pytest.mark.parametrize("shape", [6, 4])
+def test_fused_schedule_matches_oracle(sw, shape):
+    """The persistent cooperative launch runs every sweep of a chunk; each
+    replica still follows its own chain bit for bit (ragged tiles, cold and
+    hot starts, both rules), across graph re-captures and limits."""
+    reps = [(2, 0.3, 11, 0), (5, 0.6, 12, 1), (17, BETA_C, 13, 0), (64, 0.2, 14, 0),
+            (100, BETA_C, 15, 1), (128, 0.5, 16, 0), (257, 0.45, 17, 0), (300, BETA_C, 18, 0)]
+    L, beta, seed, init = (list(x) for x in zip(*reps))
+    b = sw.sw_batch_create(L, beta, seed, init, shape=shape)
+    try:
+        sw.sw_batch_set_schedule(b, sw.SW_SCHEDULE_FUSED)
+        sw.sw_batch_set_limit(b, 3, 6)            # replica 3 stops after 6 sweeps
+        sw.sw_batch_sweep(b, 3)
+        sw.sw_batch_sweep(b, 4)                   # another n: captured again
+        sw.sw_batch_sweep(b, 3)                   # replayed
+        for slot, (Lr, br, sr, ir) in enumerate(reps):
+            n = 6 if slot == 3 else 10
+            want_s, want_E, want_M = oracle_chain(Lr, br, sr, n, cold=bool(ir))
+            assert sw.sw_batch_get_sweep(b, slot) == n
+            assert np.array_equal(sw.sw_batch_spins(b, slot, Lr), want_s), slot
+            E, M = sw.sw_batch_observables(b, slot, 0, n)
+            assert np.array_equal(E, want_E) and np.array_equal(M, want_M), slot
+    finally:
+        sw.sw_batch_destroy(b)
+
+
+def test_fused_schedule_joins_leaves_and_switches(sw):
+    """Replicas join and leave between fused chunks, the assignment rule runs
+    beside the flip rule, and switching schedules mid-chain changes nothing."""
+    b = sw.sw_batch_create([33, 64, 80], [0.4, BETA_C, 0.55], [1, 2, 3], shape=6)
+    try:
+        sw.sw_batch_set_schedule(b, sw.SW_SCHEDULE_FUSED)
+        sw.sw_batch_set_rule(b, 2, sw.SW_RULE_ASSIGN)
+        sw.sw_batch_sweep(b, 5)
+        s3 = sw.sw_batch_add(b, 140, BETA_C, 4)
+        sw.sw_batch_sweep(b, 4)
+        sw.sw_batch_set_schedule(b, sw.SW_SCHEDULE_PHASES)
+        sw.sw_batch_remove(b, 1)
+        sw.sw_batch_sweep(b, 3)
+        sw.sw_batch_set_schedule(b, sw.SW_SCHEDULE_FUSED)
+        sw.sw_batch_sweep(b, 2)
+        expect = {0: (33, 0.4, 1, 14, "flip"), 2: (80, 0.55, 3, 14, "assign"), s3: (140, BETA_C, 4, 9, "flip")}
+        for slot, (Lr, br, sr, n, rule) in expect.items():
+            want_s, want_E, want_M, _ = oracle.run(Lr, br, sr, n, rule=rule)
+            assert sw.sw_batch_get_sweep(b, slot) == n
+            assert np.array_equal(sw.sw_batch_spins(b, slot, Lr), want_s), slot
+            E, M = sw.sw_batch_observables(b, slot, 0, n)
+            assert np.array_equal(E, want_E) and np.array_equal(M, want_M), slot
+    finally:
+        sw.sw_batch_destroy(b)
+
+
+def test_fused_schedule_on_the_replica_mix(sw):
+    """The 256-replica mix under the fused schedule equals the per-phase
+    schedule replica by replica (spins and whole traces)."""
+    L, beta, seed = batch_replicas()
+    out = []
+    for sched in (sw.SW_SCHEDULE_PHASES, sw.SW_SCHEDULE_FUSED):
+        b = sw.sw_batch_create(L, beta, seed)
+        try:
+            sw.sw_batch_set_schedule(b, sched)
+            sw.sw_batch_sweep(b, 6)
+            sw.sw_batch_sweep(b, 6)
+            out.append([(sw.sw_batch_spins(b, r, int(L[r])), *sw.sw_batch_observables(b, r, 0, 12))
+                        for r in range(len(L))])
+        finally:
+            sw.sw_batch_destroy(b)
+    for r, (a, f) in enumerate(zip(*out)):
+        assert all(np.array_equal(x, y) for x, y in zip(a, f)), r
+
+
+def test_fused_schedule_needs_a_matching_shape(sw):
+    b = sw.sw_batch_create([64], [0.4], [1], shape=0)   # 4-row strips in 64-row tiles
+    try:
+        with pytest.raises(sw.SWError) as ei:
+            sw.sw_batch_set_schedule(b, sw.SW_SCHEDULE_FUSED)
+        assert ei.value.status == sw.SW_EINVAL
+        with pytest.raises(sw.SWError):
+            sw.sw_batch_set_schedule(b, 7)
+    finally:
+        sw.sw_batch_destroy(b)
