@@ -592,11 +592,16 @@ def measure_batched(sw, torch, stream, n_batched: int, n_plain: int):
     starts): one batched sweep over all replicas per graph node group versus
     every replica swept alone on its own handle, one after the other."""
     from workloads import batch_replicas
+    from paper_2302_14720_gb300 import autotune
     Ls, betas, seeds = batch_replicas()
     sites = int(sum(int(x) * int(x) for x in Ls))
     chunk = 50
-    b = sw.sw_batch_create(Ls, betas, seeds, stream=stream.cuda_stream)
+    # tile shape, schedule (per-phase launches or one fused launch per chunk)
+    # and one-CTA threshold chosen by measurement on a scratch batch
+    choice = autotune.tune_batch(Ls, betas, seeds)
+    b = sw.sw_batch_create(Ls, betas, seeds, shape=choice["shape"], stream=stream.cuda_stream)
     try:
+        autotune.apply_batch(b, choice)
         sw.sw_batch_sweep(b, chunk)             # warm-up: captures the graph
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -633,7 +638,10 @@ def measure_batched(sw, torch, stream, n_batched: int, n_plain: int):
             "sites": sites, "batched_su_s": batched, "batched_sweeps": n_b,
             "batched_ms_per_sweep": ms_b / n_b, "plain_su_s": plain, "plain_sweeps": n_plain,
             "plain_ms_per_sweep": ms_p / n_plain, "ratio": batched / plain,
-            "how": "batched: sw_batch_sweep graph replays of 50 sweeps; plain: sw_sweep(n) on each of the 256 "
+            "tuned": {"shape": choice["shape"], "schedule": ["per-phase launches", "fused persistent launch"][choice["schedule"]],
+                      "small_max_L": choice["small_max_L"], "ms_per_sweep_by_candidate": choice["ms"]},
+            "how": "batched: sw_batch_sweep graph replays of 50 sweeps under the autotuned shape, schedule and "
+                   "one-CTA threshold; plain: sw_sweep(n) on each of the 256 "
                    "handles in turn; CUDA events on one stream; working set > L2 (batched), each plain "
                    "replica <= 1 MiB of spins (L2-resident)"}
 

@@ -283,6 +283,16 @@ int sw_batch_set_rule(sw_batch* b, int32_t slot, int32_t rule);
 #define SW_SCHEDULE_FUSED 1
 int sw_batch_set_schedule(sw_batch* b, int32_t schedule);
 
+/* Replicas of side L <= max_L run on the one-CTA path (a whole lattice in
+ * one CTA's shared memory, all sweeps of a chunk in one block, as sw_sweep
+ * does for small lattices): one CTA per such replica, launched before the
+ * tiled work of each chunk; the others stay on the tiles. 0 (the default)
+ * puts every replica on the tiles. The results are the same bits either
+ * way; the choice only moves time (the one-CTA path holds a whole SM for a
+ * small lattice, the tiles share SMs between replicas). max_L must be 0 or
+ * 2..181, else SW_EINVAL. Synchronises the stream when it changes. */
+int sw_batch_set_small(sw_batch* b, int32_t max_L);
+
 /* Sweep counter of the replica in `slot`. */
 int sw_batch_get_sweep(sw_batch* b, int32_t slot, uint32_t* t_out);
 

@@ -66,6 +66,7 @@ SIGNATURES = {
     "sw_batch_footprint": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "sw_batch_set_rule": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sw_batch_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sw_batch_set_small": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sw_batch_set_limit": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
     "sw_batch_get_sweep": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32)]),
     "sw_batch_observables": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _P]),
@@ -315,6 +316,10 @@ def sw_batch_set_rule(b: int, slot: int, rule: int) -> None:
 
 def sw_batch_set_schedule(b: int, schedule: int) -> None:
     _check(_lib.sw_batch_set_schedule(b, int(schedule)), "sw_batch_set_schedule")
+
+
+def sw_batch_set_small(b: int, max_L: int) -> None:
+    _check(_lib.sw_batch_set_small(b, int(max_L)), "sw_batch_set_small")
 
 
 def sw_batch_set_limit(b: int, slot: int, sweeps_left: int) -> None:

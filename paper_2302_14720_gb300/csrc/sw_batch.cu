@@ -35,6 +35,7 @@ struct Replica {
   int64_t cap = 0;     // trace capacity in sweeps
   int ntiles = 0;
   int tile0 = 0;
+  bool small = false;  // on the one-CTA path (L <= the batch's small_max_L)
   int8_t* spins = nullptr;
   sw::TileBuffers tb{};
   int64_t* em = nullptr;
@@ -79,6 +80,13 @@ struct sw_batch {
   int schedule = SW_SCHEDULE_PHASES;
   sw::GridBarrier* d_gbar = nullptr;  // the fused kernel's grid barrier
   bool fused_capture = true;          // false once capturing the cooperative launch has failed
+  // Replicas of side <= small_max_L run whole chunks on the one-CTA path
+  // (one CTA each, launched before the tiled work of a chunk); 0: none.
+  int small_max_L = 0;
+  int* d_small = nullptr;  // slots of the small replicas
+  int small_cap = 0;
+  int nsmall = 0;
+  int small_L = 0;  // largest side among them (sizes the launch's shared memory)
 };
 
 namespace {
@@ -124,6 +132,7 @@ sw::ReplicaDesc desc_of(const sw_batch* b, const Replica& r) {
   d.t_left = r.t_end - r.t;
   d.em_base = r.em;
   d.em_next = r.t - r.t_base;
+  d.small = r.small ? 1 : 0;
   return d;
 }
 
@@ -132,13 +141,36 @@ int sync_tables(sw_batch* b) {
   if (!b->dirty && !b->descs_stale) return SW_OK;
   B_CUDA(cudaStreamSynchronize(b->stream), "stream synchronize");
   if (b->dirty) {
-    std::vector<int> tile_rep;
+    std::vector<int> tile_rep, small;
+    int small_L = 0;
     for (size_t i = 0; i < b->reps.size(); ++i) {
       Replica& r = b->reps[i];
       if (!r.active) continue;
+      r.small = r.L <= b->small_max_L;
+      if (r.small) {
+        small.push_back((int)i);
+        small_L = r.L > small_L ? r.L : small_L;
+        continue;
+      }
       r.tile0 = (int)tile_rep.size();
       tile_rep.insert(tile_rep.end(), r.ntiles, (int)i);
     }
+    if ((int)small.size() > b->small_cap) {
+      if (b->d_small) cudaFree(b->d_small);
+      b->d_small = nullptr;
+      b->small_cap = 0;
+      int cap = 64;
+      while (cap < (int)small.size()) cap *= 2;
+      B_CUDA(cudaMalloc(&b->d_small, (size_t)cap * sizeof(int)), "small replica list");
+      b->small_cap = cap;
+      drop_graph(b);
+    }
+    if ((int)small.size() != b->nsmall || small_L != b->small_L) drop_graph(b);  // the launch's width and size
+    b->nsmall = (int)small.size();
+    b->small_L = small_L;
+    if (!small.empty())
+      B_CUDA(cudaMemcpy(b->d_small, small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice),
+             "small replica list upload");
     b->ntiles = (int)tile_rep.size();
     // The captured graph launches grid_tiles CTAs per phase; the tiles past
     // ntiles map to no replica and exit at once. Membership changes inside
@@ -359,7 +391,7 @@ int sw_batch_sweep(sw_batch* b, int32_t n) {
   }
   int rc = sync_tables(b);
   if (rc != SW_OK) return rc;
-  if (b->ntiles == 0) return SW_OK;
+  if (b->ntiles == 0 && b->nsmall == 0) return SW_OK;
   sw::BatchArgs ba{b->d_descs, b->d_tile_rep, b->desc_cap, b->d_err, b->d_gbar};
   const bool fused = b->schedule == SW_SCHEDULE_FUSED;
   // The n-sweep sequence: the barrier reset and one cooperative launch
@@ -367,6 +399,8 @@ int sw_batch_sweep(sw_batch* b, int32_t n) {
   // fused kernel walks the whole power-of-two bucket of batch tiles (spare
   // tiles map to no replica), like the per-phase launches.
   auto enqueue = [&]() -> cudaError_t {
+    cudaError_t es = sw::launch_small_batch(ba, b->d_small, b->nsmall, b->small_L, n, b->stream);
+    if (es != cudaSuccess || b->ntiles == 0) return es;
     if (fused) {
       cudaError_t e = cudaMemsetAsync(b->d_gbar, 0, sizeof(sw::GridBarrier), b->stream);
       if (e == cudaSuccess) e = sw::launch_batch_fused(b->shape, ba, b->grid_tiles, n, b->stream);
@@ -437,6 +471,18 @@ int sw_batch_set_schedule(sw_batch* b, int32_t schedule) {
     B_CUDA(cudaStreamSynchronize(b->stream), "stream synchronize");
     drop_graph(b);
     b->schedule = schedule;
+  }
+  return SW_OK;
+}
+
+int sw_batch_set_small(sw_batch* b, int32_t max_L) {
+  if (!b) return bfail(SW_EINVAL, "batch is NULL");
+  if (max_L != 0 && (max_L < 2 || max_L > sw::kSmallMaxL))
+    return bfail(SW_EINVAL, "max_L must be 0 or in 2..181 (a lattice the one-CTA path holds)");
+  if (max_L != b->small_max_L) {
+    B_CUDA(cudaStreamSynchronize(b->stream), "stream synchronize");
+    b->small_max_L = max_L;
+    b->dirty = true;
   }
   return SW_OK;
 }
@@ -524,6 +570,7 @@ int sw_batch_destroy(sw_batch* b) {
   if (b->d_tile_rep) cudaFree(b->d_tile_rep);
   if (b->d_err) cudaFree(b->d_err);
   if (b->d_gbar) cudaFree(b->d_gbar);
+  if (b->d_small) cudaFree(b->d_small);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return SW_OK;

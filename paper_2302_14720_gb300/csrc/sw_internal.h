@@ -100,6 +100,7 @@ struct ReplicaDesc {
   int64_t t_left;     // sweeps still to run (the replica idles at 0)
   int64_t* em_base;   // E/M trace [cap][2]
   int64_t em_next;    // trace row of the next sweep
+  int small;          // 1: runs on the one-CTA path (small_batch_kernel advances it)
 };
 
 // Arrival count and generation of the fused batch kernel's grid barrier.
@@ -163,6 +164,10 @@ struct SmallArgs {
   int* err;        // device error flag
 };
 cudaError_t launch_small(const SmallArgs& a, cudaStream_t st);
+// Batch: the replicas listed in small[0..nsmall) (sides <= max_L <=
+// kSmallMaxL) run up to n sweeps each on the one-CTA path, one CTA per
+// replica, and advance their own counters.
+cudaError_t launch_small_batch(const BatchArgs& b, const int* small, int nsmall, int max_L, int n, cudaStream_t st);
 
 // The paper's label-equivalence iteration (§2.3) over exported bonds
 // (uint8 per site, bit 0 east, bit 1 south); comparator only (sw_equiv.cu).

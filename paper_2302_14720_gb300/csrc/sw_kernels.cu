@@ -1364,7 +1364,7 @@ __global__ void batch_advance_kernel(const BatchArgs b) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= b.nrep) return;
   ReplicaDesc* D = b.descs + r;
-  if (!D->active || D->t_left <= 0) return;
+  if (!D->active || D->small || D->t_left <= 0) return;
   D->t += 1;
   D->em_next += 1;
   D->t_left -= 1;
@@ -1451,7 +1451,7 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
   if (blockIdx.x == 0) {
     for (int r = threadIdx.x; r < b.nrep; r += blockDim.x) {
       ReplicaDesc* D = b.descs + r;
-      if (!D->active || D->t_left <= 0) continue;
+      if (!D->active || D->small || D->t_left <= 0) continue;
       const int64_t m = D->t_left < nsweeps ? D->t_left : nsweeps;
       D->t += (uint32_t)m;
       D->em_next += m;

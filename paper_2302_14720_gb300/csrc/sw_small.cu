@@ -76,8 +76,8 @@ __device__ __forceinline__ T small_warp_sum(T v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kSmallThreads, 1) small_sweep_kernel(const SmallArgs a) {
-  extern __shared__ __align__(16) uint32_t smem[];
+// The n sweeps of one lattice by the whole CTA (smem: small_smem_bytes(L)).
+__device__ __forceinline__ void small_body(const SmallArgs& a, uint32_t* smem) {
   constexpr int NT = kSmallThreads, NW = NT / 32;
   __shared__ long long s_red[2][NW];
   __shared__ uint16_t s_rootq[NW][64];  // roots waiting for their draw
@@ -289,6 +289,40 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_sweep_kernel(const Sma
   }
 }
 
+__global__ void __launch_bounds__(kSmallThreads, 1) small_sweep_kernel(const SmallArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  small_body(a, smem);
+}
+
+// Batch replicas on the one-CTA path: CTA i runs replica small[i] for the
+// sweeps of this chunk it has left (at most n), writes its trace rows and
+// then advances its counter, trace row and sweeps left itself (the tiled
+// schedule's counter advance skips these replicas).
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    small_batch_kernel(const BatchArgs b, const int* small, int n) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  ReplicaDesc* D = b.descs + small[blockIdx.x];
+  if (!D->active || D->t_left <= 0) return;
+  const int m = D->t_left < n ? (int)D->t_left : n;
+  SmallArgs a;
+  a.L = D->a.g.L;
+  a.thr = D->a.thr;
+  a.rule = D->a.rule;
+  a.t0 = D->t;
+  a.n = m;
+  a.ks = D->a.ks;
+  a.spins = D->a.spins_out;
+  a.em = D->em_base + 2 * D->em_next;
+  a.err = D->a.tb.err;
+  small_body(a, smem);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    D->t += (uint32_t)m;
+    D->em_next += m;
+    D->t_left -= m;
+  }
+}
+
 size_t small_smem_bytes(int L) {
   const size_t N = (size_t)L * L, WPL = (size_t)(L + 31) / 32, RWN = (size_t)L * WPL, DW = (N + 31) / 32;
   return (3 * RWN + DW) * sizeof(uint32_t) + N * sizeof(uint16_t);
@@ -308,6 +342,20 @@ cudaError_t launch_small(const SmallArgs& a, cudaStream_t st) {
     attr_done = true;
   }
   small_sweep_kernel<<<1, kSmallThreads, small_smem_bytes(a.L), st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_batch(const BatchArgs& b, const int* small, int nsmall, int max_L, int n, cudaStream_t st) {
+  if (nsmall <= 0 || n <= 0) return cudaSuccess;
+  if (max_L < 2 || max_L > kSmallMaxL) return cudaErrorInvalidValue;
+  static bool attr_done = false;
+  if (!attr_done) {
+    const cudaError_t e = cudaFuncSetAttribute(small_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)small_smem_bytes(kSmallMaxL));
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  small_batch_kernel<<<nsmall, kSmallThreads, small_smem_bytes(max_L), st>>>(b, small, n);
   return cudaGetLastError();
 }
 

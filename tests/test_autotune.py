@@ -32,3 +32,30 @@ def test_tune_and_table_round_trip(tmp_path, monkeypatch):
     got = autotune.load(str(path), device="GB300-test")
     assert installed == {10: 1, 13: 0} and got[13]["L"] == 8192
     assert autotune.load(str(path), device="other") == {}
+
+
+def test_batch_candidates_offer_the_fused_schedule_only_where_it_exists():
+    c = autotune.batch_candidates([6, 0], small=(0, 64))
+    assert (6, sw.SW_SCHEDULE_FUSED, 64) in c and (6, sw.SW_SCHEDULE_PHASES, 0) in c
+    assert all(sched == sw.SW_SCHEDULE_PHASES for sh, sched, _ in c if sh == 0)   # 4-row strips in 64-row tiles
+    assert len(c) == 2 * 2 + 1 * 2
+
+
+def test_tune_batch_picks_the_fastest_and_skips_refused_candidates():
+    fake = {(6, 0, 0): 0.48, (6, 1, 0): 0.61, (6, 0, 64): 0.47, (4, 0, 0): 0.50}
+
+    def timer(sh, sc, sm):
+        if (sh, sc, sm) not in fake:
+            raise sw.SWError(sw.SW_EINVAL, "sw_batch_set_schedule", "refused")
+        return fake[(sh, sc, sm)]
+    got = autotune.tune_batch([64], [0.4], [1], candidates=list(fake) + [(0, 1, 0)], timer=timer)
+    assert (got["shape"], got["schedule"], got["small_max_L"]) == (6, 0, 64)
+    assert got["ms_per_sweep"] == 0.47 and len(got["ms"]) == 4
+
+
+def test_apply_batch_sets_schedule_and_threshold(monkeypatch):
+    calls = []
+    monkeypatch.setattr(autotune, "sw_batch_set_schedule", lambda b, s: calls.append(("schedule", b, s)))
+    monkeypatch.setattr(autotune, "sw_batch_set_small", lambda b, m: calls.append(("small", b, m)))
+    autotune.apply_batch(7, {"shape": 6, "schedule": 1, "small_max_L": 64})
+    assert calls == [("schedule", 7, 1), ("small", 7, 64)]

@@ -231,3 +231,51 @@ def test_fused_schedule_needs_a_matching_shape(sw):
             sw.sw_batch_set_schedule(b, 7)
     finally:
         sw.sw_batch_destroy(b)
+
+
+# ------------------------------------------- small replicas on the one-CTA path
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_small_replicas_on_the_one_cta_path(sw, schedule):
+    """Replicas up to the threshold run whole chunks in one CTA each, beside
+    tiled replicas; every chain stays the oracle's (limits, both rules,
+    cold and hot starts, ragged sides, a threshold change mid-run)."""
+    reps = [(2, 0.3, 21, 0), (17, BETA_C, 22, 1), (64, 0.2, 23, 0), (100, BETA_C, 24, 0),
+            (181, 0.45, 25, 0), (182, BETA_C, 26, 0), (300, 0.5, 27, 1)]
+    L, beta, seed, init = (list(x) for x in zip(*reps))
+    b = sw.sw_batch_create(L, beta, seed, init, shape=6)
+    try:
+        sw.sw_batch_set_schedule(b, schedule)
+        sw.sw_batch_set_small(b, 181)
+        sw.sw_batch_set_rule(b, 3, sw.SW_RULE_ASSIGN)
+        sw.sw_batch_set_limit(b, 1, 5)
+        sw.sw_batch_sweep(b, 4)
+        sw.sw_batch_sweep(b, 3)
+        sw.sw_batch_set_small(b, 64)             # 100 and 181 move back to the tiles
+        sw.sw_batch_sweep(b, 3)
+        for slot, (Lr, br, sr, ir) in enumerate(reps):
+            n = 5 if slot == 1 else 10
+            rule = "assign" if slot == 3 else "flip"
+            want_s, want_E, want_M, _ = oracle.run(Lr, br, sr, n, cold=bool(ir), rule=rule)
+            assert sw.sw_batch_get_sweep(b, slot) == n
+            assert np.array_equal(sw.sw_batch_spins(b, slot, Lr), want_s), slot
+            E, M = sw.sw_batch_observables(b, slot, 0, n)
+            assert np.array_equal(E, want_E) and np.array_equal(M, want_M), slot
+        with pytest.raises(sw.SWError):
+            sw.sw_batch_set_small(b, 182)
+    finally:
+        sw.sw_batch_destroy(b)
+
+
+def test_only_small_replicas(sw):
+    b = sw.sw_batch_create([16, 40], [BETA_C, 0.5], [31, 32], shape=6)
+    try:
+        sw.sw_batch_set_small(b, 64)
+        sw.sw_batch_sweep(b, 7)
+        for slot, (Lr, br, sr) in enumerate([(16, BETA_C, 31), (40, 0.5, 32)]):
+            want_s, want_E, want_M = oracle_chain(Lr, br, sr, 7)
+            assert np.array_equal(sw.sw_batch_spins(b, slot, Lr), want_s)
+            E, M = sw.sw_batch_observables(b, slot, 0, 7)
+            assert np.array_equal(E, want_E) and np.array_equal(M, want_M)
+    finally:
+        sw.sw_batch_destroy(b)
