@@ -214,13 +214,17 @@ int sw_bonds(sw_lattice* h, uint8_t* out_host);
  * phase launch of sw_sweep is bracketed by CUDA events on the handle's
  * stream (accumulators cleared); enable = 0 stops recording. Phases:
  * 0 = bonds + tile-local clusters, 1 = cross-tile merge, 2 = flips + E/M,
- * 3 = cluster statistics. Not part of the paper: measurement support. */
+ * 3 = cluster statistics, 4 = flips + E/M of a sweep together with the bonds
+ * and tile-local clusters of the next sweep (the one launch sw_sweep uses
+ * for both when statistics are off; a call whose previous call ended with
+ * it starts at phase 1). Not part of the paper: measurement support. */
+#define SW_TIMING_PHASES 5
 int sw_timing(sw_lattice* h, int32_t enable);
 
-/* Synchronise, then report for each of the 4 phases the summed device time
- * in milliseconds (ms_out[4]) and the number of kernel launches
- * (launches_out[4]) recorded since sw_timing(h, 1). Either pointer may be
- * NULL. */
+/* Synchronise, then report for each of the SW_TIMING_PHASES phases the
+ * summed device time in milliseconds (ms_out[SW_TIMING_PHASES]) and the
+ * number of kernel launches (launches_out[SW_TIMING_PHASES]) recorded since
+ * sw_timing(h, 1). Either pointer may be NULL. */
 int sw_timing_read(sw_lattice* h, double* ms_out, int64_t* launches_out);
 
 /* ---------------------------------------------------------------------------

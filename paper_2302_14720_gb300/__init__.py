@@ -32,6 +32,7 @@ SW_RULE_FLIP = 0
 SW_RULE_ASSIGN = 1
 SW_SCHEDULE_PHASES = 0
 SW_SCHEDULE_FUSED = 1
+SW_TIMING_PHASES = 5
 SW_HIST_WORDS = 34
 
 _STATUS_NAMES = {SW_EINVAL: "SW_EINVAL", SW_ENOMEM: "SW_ENOMEM", SW_ECUDA: "SW_ECUDA",
@@ -243,9 +244,10 @@ def sw_timing(h: int, enable: bool) -> None:
 
 
 def sw_timing_read(h: int):
-    """(ms per phase float64[4], launches per phase int64[4]) since sw_timing(h, True)."""
-    ms = np.zeros(4, np.float64)
-    n = np.zeros(4, np.int64)
+    """(ms per phase float64[5], launches per phase int64[5]) since sw_timing(h, True);
+    phase 4 is a sweep's flips together with the next sweep's bonds and tile clusters."""
+    ms = np.zeros(SW_TIMING_PHASES, np.float64)
+    n = np.zeros(SW_TIMING_PHASES, np.int64)
     _check(_lib.sw_timing_read(h, _host_ptr(ms), _host_ptr(n)), "sw_timing_read")
     return ms, n
 

@@ -49,8 +49,9 @@ def time_shape(L: int, shape: int, beta: float = 0.44068679, sweeps: int = 5, wa
         lat.sweep(sweeps)
         ms, n = sw_timing_read(lat.h)
         lat.observables(0, 1)  # checks the device error flag
-    per = ms / np.maximum(n, 1)
-    return float(per[:3].sum())
+    # every kernel of the timed sweeps (a sweep's phase 3 may carry the next
+    # sweep's phase 1), over the sweeps
+    return float(ms.sum() / sweeps)
 
 
 def choose(times: dict[int, float]) -> int:

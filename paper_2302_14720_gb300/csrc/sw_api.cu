@@ -104,6 +104,14 @@ struct sw_lattice {
   sw::Geometry g{};
   sw::KeySchedule ks{};
   sw::TileBuffers tb{};
+  // A second set of the tables that neighbouring tiles read (border slots,
+  // slot counts, slot nodes): sweep t uses set t & 1, so that phase 3 of
+  // sweep t and phase 1 of sweep t + 1 can run in one launch (phase31).
+  uint16_t* bslot2 = nullptr;
+  int32_t* nslots2 = nullptr;
+  uint64_t* nodes2 = nullptr;
+  bool fuse = false;       // the tile shape has the phase31 launch
+  bool p1_ready = false;   // phase 1 of sweep t (the current counter) has run on the current spins
   int8_t* spins = nullptr;
   uint32_t* csize = nullptr;
   int64_t* em = nullptr;    // [cap][2]
@@ -122,14 +130,15 @@ struct sw_lattice {
   };
   std::vector<Mark> marks;
   std::vector<cudaEvent_t> event_pool;
-  double phase_ms[4] = {0, 0, 0, 0};
-  int64_t phase_launches[4] = {0, 0, 0, 0};
+  double phase_ms[SW_TIMING_PHASES] = {0, 0, 0, 0, 0};
+  int64_t phase_launches[SW_TIMING_PHASES] = {0, 0, 0, 0, 0};
 };
 
 namespace {
 
 void free_all(sw_lattice* h) {
   void* ptrs[] = {h->spins, h->tb.tbits, h->tb.roots, h->tb.bmask, h->tb.rbits, h->tb.nodes, h->tb.bslot, h->tb.bbits, h->tb.nslots, h->tb.err,
+                  h->bslot2, h->nslots2, h->nodes2,
                   h->csize, h->em, h->hist, h->label_buf, h->bond_buf, h->ref_buf, h->le_flag, h->staging,
                   h->check_flag};
   for (void* p : ptrs)
@@ -180,14 +189,22 @@ cudaError_t drain_marks(sw_lattice* h) {
   return cudaSuccess;
 }
 
-sw::SweepArgs args_of(const sw_lattice* h) {
+// The arguments of sweep t (default: the current counter); an odd sweep uses
+// the second set of neighbour-read tables when the handle has one.
+sw::SweepArgs args_of(const sw_lattice* h, int64_t t = -1) {
+  if (t < 0) t = h->t;
   sw::SweepArgs a{};
   a.g = h->g;
   a.thr = h->thr;
-  a.t = (uint32_t)h->t;
+  a.t = (uint32_t)t;
   a.rule = (uint32_t)h->rule;
   a.ks = h->ks;
   a.tb = h->tb;
+  if (h->fuse && (t & 1)) {
+    a.tb.bslot = h->bslot2;
+    a.tb.nslots = h->nslots2;
+    a.tb.nodes = h->nodes2;
+  }
   a.spins_in = h->spins;
   a.spins_out = h->spins;
   return a;
@@ -248,6 +265,7 @@ int range_ok(const sw_lattice* h, int64_t first, int64_t count) {
 
 // Phases 1-2 for the current state and counter (bonds, tile clusters, merge).
 int run_clusters(sw_lattice* h, sw::SweepArgs& a) {
+  h->p1_ready = false;  // phase 2 below changes the nodes a carried-over phase 1 left
   a.em = nullptr;
   a.hist = nullptr;
   a.csize = nullptr;
@@ -316,6 +334,10 @@ int sw_create(int32_t L, double beta, uint64_t seed, int32_t init, void* stream,
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.nslots, ntiles * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.err, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->csize, ntiles * ts.max_slots() * sizeof(uint32_t));
+  h->fuse = sw::batch_fused_supported(h->shape);
+  if (e == cudaSuccess && h->fuse) e = cudaMalloc(&h->nodes2, ntiles * ts.max_slots() * sizeof(uint64_t));
+  if (e == cudaSuccess && h->fuse) e = cudaMalloc(&h->bslot2, ntiles * ts.boundary_sites() * sizeof(uint16_t));
+  if (e == cudaSuccess && h->fuse) e = cudaMalloc(&h->nslots2, ntiles * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->tb.err, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) e = sw::launch_init(h->spins, L, seed, init == SW_INIT_COLD, h->stream);
   if (e != cudaSuccess) {
@@ -346,7 +368,8 @@ int sw_sweep(sw_lattice* h, int32_t n) {
   if (!h) return fail(SW_EINVAL, "handle is NULL");
   if (n < 0) return fail(SW_EINVAL, "n must be >= 0");
   if (n == 0) return SW_OK;
-  int rc = ensure_trace(h, h->t - h->t_base + n);
+  // one row more: a carried-over phase 1 zeroes the next sweep's row
+  int rc = ensure_trace(h, h->t - h->t_base + n + 1);
   if (rc != SW_OK) return rc;
   const sw::TileShape ts = sw::shape_of(h->shape);
   (void)ts;
@@ -363,21 +386,41 @@ int sw_sweep(sw_lattice* h, int32_t n) {
     s.em = h->em + 2 * (h->t - h->t_base);
     s.err = h->tb.err;
     SW_CUDA(timed_phase(h, 0, [&] { return sw::launch_small(s, h->stream); }), "small-lattice sweep launch");
+    h->p1_ready = false;
     h->t += n;
     return SW_OK;
   }
+  // Without statistics and on a shape that has it, phase 3 of a sweep and
+  // phase 1 of the next one run as one launch (phase31), including after the
+  // call's last sweep: the next call then starts at phase 2. Every state
+  // change (sw_set_state*, sw_histogram, a call that runs phase 1 itself)
+  // drops that carried-over phase 1.
+  const bool fused = h->fuse && !h->hist_on;
+  if (!fused && h->p1_ready) h->p1_ready = false;
   for (int32_t k = 0; k < n; ++k) {
     sw::SweepArgs a = args_of(h);
     const int64_t row = h->t - h->t_base;
     a.em = h->em + 2 * row;
     a.hist = h->hist + SW_HIST_WORDS * row;
     a.csize = h->hist_on ? h->csize : nullptr;
-    SW_CUDA(timed_phase(h, 0, [&] { return sw::launch_phase1(h->shape, a, h->stream); }), "phase 1 launch");
+    if (!h->p1_ready)
+      SW_CUDA(timed_phase(h, 0, [&] { return sw::launch_phase1(h->shape, a, h->stream); }), "phase 1 launch");
+    h->p1_ready = false;
     SW_CUDA(timed_phase(h, 1, [&] { return sw::launch_phase2(h->shape, a, h->stream); }), "phase 2 launch");
     if (!h->hist_on) a.hist = nullptr;
-    SW_CUDA(timed_phase(h, 2, [&] { return sw::launch_phase3(h->shape, a, false, h->stream); }), "phase 3 launch");
-    if (h->hist_on)
-      SW_CUDA(timed_phase(h, 3, [&] { return sw::launch_phase4(h->shape, a, h->stream); }), "phase 4 launch");
+    if (fused) {
+      sw::SweepArgs a1 = args_of(h, h->t + 1);
+      a1.em = h->em + 2 * (row + 1);  // zeroed by the next sweep's phase 1 (the trace has room)
+      a1.hist = nullptr;
+      a1.csize = nullptr;
+      SW_CUDA(timed_phase(h, 4, [&] { return sw::launch_phase31(h->shape, a, a1, h->stream); }),
+              "phase 3 + next phase 1 launch");
+      h->p1_ready = true;
+    } else {
+      SW_CUDA(timed_phase(h, 2, [&] { return sw::launch_phase3(h->shape, a, false, h->stream); }), "phase 3 launch");
+      if (h->hist_on)
+        SW_CUDA(timed_phase(h, 3, [&] { return sw::launch_phase4(h->shape, a, h->stream); }), "phase 4 launch");
+    }
     h->t += 1;
   }
   return SW_OK;
@@ -421,6 +464,7 @@ int sw_set_rule(sw_lattice* h, int32_t rule) {
 
 int sw_histogram(sw_lattice* h, int32_t enable) {
   if (!h) return fail(SW_EINVAL, "handle is NULL");
+  if (h->hist_on != (enable != 0)) h->p1_ready = false;  // phase 1 zeroes the size counters with statistics on
   h->hist_on = enable != 0;
   return SW_OK;
 }
@@ -507,6 +551,7 @@ int sw_set_state_async(sw_lattice* h, const int8_t* spins, uint32_t t) {
   SW_CUDA(cudaGetLastError(), "restore launch");
   h->t = t;
   h->t_base = t;
+  h->p1_ready = false;
   return SW_OK;
 }
 
@@ -534,6 +579,7 @@ int sw_set_state(sw_lattice* h, const int8_t* spins, uint32_t t, int32_t in_is_d
   }
   h->t = t;
   h->t_base = t;
+  h->p1_ready = false;
   return SW_OK;
 }
 
@@ -562,7 +608,7 @@ int sw_timing(sw_lattice* h, int32_t enable) {
   if (enable) {
     SW_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
     SW_CUDA(drain_marks(h), "timing events");
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < SW_TIMING_PHASES; ++k) {
       h->phase_ms[k] = 0.0;
       h->phase_launches[k] = 0;
     }
@@ -575,7 +621,7 @@ int sw_timing_read(sw_lattice* h, double* ms_out, int64_t* launches_out) {
   if (!h) return fail(SW_EINVAL, "handle is NULL");
   SW_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
   SW_CUDA(drain_marks(h), "timing events");
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < SW_TIMING_PHASES; ++k) {
     if (ms_out) ms_out[k] = h->phase_ms[k];
     if (launches_out) launches_out[k] = h->phase_launches[k];
   }
@@ -597,6 +643,7 @@ int sw_labels_equivalence(sw_lattice* h, int32_t* out, int32_t out_is_device, in
   a.em = nullptr;
   a.hist = nullptr;
   a.csize = nullptr;
+  h->p1_ready = false;
   SW_CUDA(sw::launch_phase1(h->shape, a, h->stream), "phase 1 launch");
   SW_CUDA(sw::launch_export_bonds(h->shape, a, h->bond_buf, h->stream), "bond export launch");
   int its = 0;

@@ -144,6 +144,10 @@ cudaError_t launch_batch_advance(const BatchArgs& b, cudaStream_t st);
 // advances the replicas' counters itself. Only shapes whose phases 1 and 3
 // take the same block (TH == 32 H) have it: batch_fused_supported.
 bool batch_fused_supported(int shape);
+// Phase 3 of sweep t (a3) and phase 1 of sweep t + 1 (a1) in one launch, the
+// new spins handed over in shared memory (flip or assignment rule, no
+// statistics). Same shapes as batch_fused_supported.
+cudaError_t launch_phase31(int shape, const SweepArgs& a3, const SweepArgs& a1, cudaStream_t st);
 cudaError_t launch_batch_fused(int shape, const BatchArgs& b, int ntiles, int nsweeps, cudaStream_t st);
 
 // Whole sweeps of one small lattice in one CTA (sw_small.cu). 181^2 < 2^15,

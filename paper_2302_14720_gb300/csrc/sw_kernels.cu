@@ -528,7 +528,10 @@ struct P1Shared {
   uint32_t wsum[33];
 };
 
-template <int WPR, int TH, int H, bool BATCH>
+// SPINS_GIVEN: the caller has put the spin words in S.sd[0] and the halo's
+// spins in S.bb (east column, south row), as phase 3 of the previous sweep
+// leaves them (phase31_kernel); the spins are not read from global memory.
+template <int WPR, int TH, int H, bool BATCH, bool SPINS_GIVEN = false>
 __device__ __forceinline__ void phase1_body(P1Shared<WPR, TH, H>& S, const SweepArgs& a0, const BatchArgs& bat,
                                             int T, int k) {
   using Tl = Tile<WPR, TH, H>;
@@ -561,34 +564,39 @@ __device__ __forceinline__ void phase1_body(P1Shared<WPR, TH, H>& S, const Sweep
   uint32_t* hE = s_bb + Tl::OFF_HE;
   uint32_t* hS = s_bb + Tl::OFF_HS;
 
-  for (int i = tid; i < BBW; i += NT) s_bb[i] = 0u;
+  if (SPINS_GIVEN) {
+    for (int i = tid; i < Tl::OFF_HE; i += NT) s_bb[i] = 0u;  // out-going bond bits; the halo is given
+    __syncthreads();
+  } else {
+    for (int i = tid; i < BBW; i += NT) s_bb[i] = 0u;
 
-  // ---- spins: thread tid takes row words tid, tid + NT, ... (row-major)
+    // ---- spins: thread tid takes row words tid, tid + NT, ... (row-major)
 #pragma unroll
-  for (int i = 0; i < RPL; ++i) {
-    const int rw = tid + NT * i, y = rw / WPR, w = rw % WPR;
-    const int nbw = max(0, min(32, P.ncols - 32 * w));
-    uint32_t sb = 0u;
-    if (y < P.nrows && nbw)
-      sb = load_spin_bits(a.spins_in + (size_t)(P.y0 + y) * L + P.x0 + 32 * w, nbw, g.aligned16);
-    s_spin[y][w] = sb;
-  }
-  __syncthreads();
+    for (int i = 0; i < RPL; ++i) {
+      const int rw = tid + NT * i, y = rw / WPR, w = rw % WPR;
+      const int nbw = max(0, min(32, P.ncols - 32 * w));
+      uint32_t sb = 0u;
+      if (y < P.nrows && nbw)
+        sb = load_spin_bits(a.spins_in + (size_t)(P.y0 + y) * L + P.x0 + 32 * w, nbw, g.aligned16);
+      s_spin[y][w] = sb;
+    }
+    __syncthreads();
 
-  // ---- east halo column and south halo row (periodic wrap)
-  const int xe = (P.x0 + P.ncols) % L;
-  const int ys = (P.y0 + P.nrows) % L;
-  for (int b0 = warp0; b0 < TH; b0 += NT) {
-    const int y = b0 + lane;
-    const bool bit = y < P.nrows && __ldcg(a.spins_in + (size_t)(P.y0 + y) * L + xe) < 0;
-    const uint32_t m = __ballot_sync(0xffffffffu, bit);
-    if (lane == 0) hE[b0 >> 5] = m;
+    // ---- east halo column and south halo row (periodic wrap)
+    const int xe = (P.x0 + P.ncols) % L;
+    const int ys = (P.y0 + P.nrows) % L;
+    for (int b0 = warp0; b0 < TH; b0 += NT) {
+      const int y = b0 + lane;
+      const bool bit = y < P.nrows && __ldcg(a.spins_in + (size_t)(P.y0 + y) * L + xe) < 0;
+      const uint32_t m = __ballot_sync(0xffffffffu, bit);
+      if (lane == 0) hE[b0 >> 5] = m;
+    }
+    for (int ww = tid; ww < WPR; ww += NT) {
+      const int nbw = max(0, min(32, P.ncols - 32 * ww));
+      hS[ww] = nbw ? load_spin_bits(a.spins_in + (size_t)ys * L + P.x0 + 32 * ww, nbw, g.aligned16) : 0u;
+    }
+    __syncthreads();
   }
-  for (int ww = tid; ww < WPR; ww += NT) {
-    const int nbw = max(0, min(32, P.ncols - 32 * ww));
-    hS[ww] = nbw ? load_spin_bits(a.spins_in + (size_t)ys * L + P.x0 + 32 * ww, nbw, g.aligned16) : 0u;
-  }
-  __syncthreads();
 
   // ---- bonds (§2.1), same row words as the spins
   uint32_t* tb = a.tb.tbits + (size_t)P.tile * 3 * RW;
@@ -1460,6 +1468,44 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
   }
 }
 
+// Phase 3 of sweep t and phase 1 of sweep t + 1 of one tile, in one CTA.
+// Phase 3 leaves the tile's new spin words and its halo sites' new spins in
+// shared memory, and these are the first things phase 1 of the next sweep
+// reads, so they are handed over there instead of through global memory (the
+// int8 spins are still written: the state stays in HBM). a3 and a1 are the
+// two sweeps' arguments; they name different border-slot, slot-count and
+// node tables (by sweep parity), because other tiles' phase 3 of sweep t
+// still reads this tile's tables of sweep t while this CTA writes those of
+// sweep t + 1. Every other table a tile writes is read by that tile alone.
+template <int WPR, int TH, int H>
+__global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
+    phase31_kernel(const SweepArgs a3, const SweepArgs a1) {
+  using Tl = Tile<WPR, TH, H>;
+  constexpr int NT = 32 * WPR, RPL = TH / 32, NHE = TH / 32, NH = TH / 32 + Tl::TW / 32;
+  static_assert(Tl::NT == NT, "phases 1 and 3 run the same block");
+  __shared__ FusedShared<WPR, TH, H> U;
+  const int tid = threadIdx.x;
+  if (!phase3_body<WPR, TH, H, 0, false>(U.p3, nullptr, a3, BatchArgs{}, blockIdx.x, 0)) return;
+  uint32_t words[RPL], halo = 0u;
+#pragma unroll
+  for (int i = 0; i < RPL; ++i) {
+    const int rw = tid + NT * i;
+    words[i] = U.p3.snew[rw / WPR][rw % WPR];
+  }
+  if (tid < NHE) halo = U.p3.hEnew[tid];
+  else if (tid < NH) halo = U.p3.hSnew[tid - NHE];
+  __syncthreads();  // the two sweeps' shared memory overlaps
+#pragma unroll
+  for (int i = 0; i < RPL; ++i) {
+    const int rw = tid + NT * i;
+    U.p1.sd[0][rw / WPR][rw % WPR] = words[i];
+  }
+  if (tid < NHE) U.p1.bb[Tl::OFF_HE + tid] = halo;
+  else if (tid < NH) U.p1.bb[Tl::OFF_HS + tid - NHE] = halo;
+  __syncthreads();
+  phase1_body<WPR, TH, H, false, true>(U.p1, a1, BatchArgs{}, blockIdx.x, 0);
+}
+
 template <int WPR, int TH, int H>
 cudaError_t launch_fused_shape(const BatchArgs& b, int ntiles, int nsweeps, cudaStream_t st) {
   auto kern = batch_fused_kernel<WPR, TH, H>;
@@ -1642,6 +1688,19 @@ cudaError_t launch_batch_advance(const BatchArgs& b, cudaStream_t st) {
   if (b.nrep <= 0) return cudaSuccess;
   batch_advance_kernel<<<(b.nrep + 127) / 128, 128, 0, st>>>(b);
   return cudaGetLastError();
+}
+
+cudaError_t launch_phase31(int shape, const SweepArgs& a3, const SweepArgs& a1, cudaStream_t st) {
+  const int ntiles = a3.g.tiles_x * a3.g.tiles_y;
+  switch (shape) {
+    case 4:
+      phase31_kernel<shape_of(4).wpr, shape_of(4).th, shape_of(4).h><<<ntiles, 32 * shape_of(4).wpr, 0, st>>>(a3, a1);
+      return cudaGetLastError();
+    case 6:
+      phase31_kernel<shape_of(6).wpr, shape_of(6).th, shape_of(6).h><<<ntiles, 32 * shape_of(6).wpr, 0, st>>>(a3, a1);
+      return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
 }
 
 bool batch_fused_supported(int shape) {
