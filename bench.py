@@ -78,6 +78,13 @@ PHASE_BYTES_PER_TILE[4] = PHASE_BYTES_PER_TILE[0] + PHASE_BYTES_PER_TILE[2] - (T
 PHASE_NAMES = {0: "phase1_bonds_tile_ccl", 1: "phase2_merge_resolve", 2: "phase3_flip_em", 3: "phase4_hist",
                4: "phase3_with_next_phase1"}
 SWEEP_MODEL_BYTES_PER_SITE = 10  # read spins, write+read int32 labels, write spins
+# q-state Potts sweep (§6) on the same tiles: phase 1 and phase 2 + resolve
+# as for Ising (the state bytes take the place of the spins); phase 3 reads
+# the 16-bit tile roots, border-root and root masks, slot count, the tile's
+# slot states and the halo's slots and slot states, and writes the states.
+MS = 2 * (TW + TH)
+POTTS_BYTES_PER_TILE = (PHASE_BYTES_PER_TILE[0] + PHASE_BYTES_PER_TILE[1]
+                        + 2 * TW * TH + 2 * 4 * RW + 4 + MS + 3 * (TH + TW) + TW * TH)
 
 
 def peaks():
@@ -570,13 +577,19 @@ def measure_other_configs(sw, torch, stream, flush):
             ms_le = timed_sweeps(torch, stream, lambda: sw.sw_labels_equivalence(lat.h, Lc, buf.data_ptr()), 1)
         out["labels_union_find_vs_equivalence"][f"L{Lc}"] = {
             "union_find_ms": ms_uf, "label_equivalence_ms": ms_le, "iterations": its, "speedup": ms_le / ms_uf}
-    # q = 3 Potts at its critical coupling ln(1 + sqrt 3)
-    with sw.Potts(1024, 3, 1.0050833, 4, stream=stream.cuda_stream) as pt:
-        pt.sweep(10)
-        n = 200
-        ms = timed_sweeps(torch, stream, lambda: pt.sweep(n), n)
-        pt.observables(10, n)
-    out["potts_q3_L1024_betac"] = {"su_s": 1024 * 1024 * n / (ms / 1e3), "us_per_sweep": 1e3 * ms / n, "sweeps": n}
+    # q = 3 Potts at its critical coupling ln(1 + sqrt 3), on the tiled path
+    peak_gbs, peak_kind = peaks()
+    for Lq, n in ((1024, 200), (8192, 40)):
+        with sw.Potts(Lq, 3, 1.0050833, 4, stream=stream.cuda_stream) as pt:
+            pt.sweep(10)
+            ms = timed_sweeps(torch, stream, lambda: pt.sweep(n), n)
+            pt.observables(10, n)
+        ntiles = -(-Lq // TW) * -(-Lq // TH)
+        gbs = POTTS_BYTES_PER_TILE * ntiles / (ms / n / 1e3) / 1e9
+        out[f"potts_q3_L{Lq}_betac"] = {
+            "su_s": Lq * Lq * n / (ms / 1e3), "us_per_sweep": 1e3 * ms / n, "sweeps": n,
+            "bytes_per_site": POTTS_BYTES_PER_TILE / (TW * TH), "achieved_gbs": gbs,
+            "frac_of_hbm": gbs / peak_gbs, "peak": f"{peak_gbs:.0f} GB/s ({peak_kind})"}
     # O(4) phi^4 multicluster updates at the paper's kappa = 0.304 (§5's
     # second table: L = 16..28, 10^4 updates)
     out["phi4_kappa0.304"] = {}

@@ -63,6 +63,7 @@ struct TileBuffers {
   uint32_t* bbits;   // [ntiles][bbits_words]: E-out bonds, S-out bonds, east halo spins, south halo spins
   int32_t* nslots;   // [ntiles]
   int* err;          // device error flag
+  uint8_t* nval;     // Potts only, [ntiles * max_slots]: new state of each slot's cluster (resolve -> phase 3)
 };
 
 struct Geometry {
@@ -76,6 +77,7 @@ struct SweepArgs {
   uint32_t thr;        // bond threshold (C3)
   uint32_t t;          // sweep counter (C5, C6)
   uint32_t rule;       // new spins: 0 flip each cluster with probability 1/2 (C6), 1 assign a fresh spin (§2.4)
+  uint32_t q;          // 0: Ising spins +-1; q >= 2: Potts states 0..q-1 in spins_in / spins_out (§6)
   KeySchedule ks;      // Philox key schedule of the seed (C4)
   TileBuffers tb;
   const int8_t* spins_in;
@@ -180,5 +182,13 @@ cudaError_t run_label_equivalence(const uint8_t* bonds, int L, int32_t* lab, int
                                   int max_iter, int* iterations, cudaStream_t st);
 // Debug: expand the stored bond bits into uint8 [L][L] (bit0 east, bit1 south).
 cudaError_t launch_export_bonds(int shape, const SweepArgs& a, uint8_t* out, cudaStream_t st);
+
+// q-state Potts sweeps (§6) on the 128x64 tile shape: phase 1 bonds equal
+// states, phase 2 (launch_phase2) is the Ising one with resolve drawing each
+// border cluster's new state into tb.nval, and phase 3 assigns the states and
+// sums E, M. Labels come from launch_phase3's labels mode. a.q >= 2.
+constexpr int kPottsShape = 6;
+cudaError_t launch_potts_phase1(const SweepArgs& a, cudaStream_t st);
+cudaError_t launch_potts_phase3(const SweepArgs& a, cudaStream_t st);
 
 }  // namespace sw

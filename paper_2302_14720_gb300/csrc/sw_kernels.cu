@@ -105,6 +105,40 @@ __device__ __forceinline__ void store_spin_bits(int8_t* p, uint32_t bits, int nb
   for (int k = 0; k < nb; ++k) p[k] = ((bits >> k) & 1u) ? (int8_t)-1 : (int8_t)1;
 }
 
+// §6 (q-state Potts): bit b of eqE / eqS is set iff site x0 + b of `row`
+// has the same state as its east neighbour (column x0 + b + 1 mod L) / as
+// the site below it (`rowS`, the next row mod L); nb valid columns. A whole
+// 16-byte aligned word compares four states per instruction.
+__device__ __forceinline__ void potts_equal_bits(const int8_t* row, const int8_t* rowS, int x0, int nb, int L,
+                                                 bool vec, uint32_t& eqE, uint32_t& eqS) {
+  if (vec && nb == 32) {
+    const uint4 a0 = *reinterpret_cast<const uint4*>(row + x0), a1 = *reinterpret_cast<const uint4*>(row + x0 + 16);
+    const uint4 b0 = *reinterpret_cast<const uint4*>(rowS + x0), b1 = *reinterpret_cast<const uint4*>(rowS + x0 + 16);
+    const uint32_t A[9] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w,
+                           (uint32_t)(uint8_t)row[x0 + 32 == L ? 0 : x0 + 32]};
+    const uint32_t B[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    uint32_t e = 0u, d = 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      // the four east neighbours of word k's states: bytes 1-3 of word k, byte 0 of word k + 1
+      e |= sign_bits4(__vcmpeq4(A[k], __funnelshift_r(A[k], A[k + 1], 8))) << (4 * k);
+      d |= sign_bits4(__vcmpeq4(A[k], B[k])) << (4 * k);
+    }
+    eqE = e;
+    eqS = d;
+    return;
+  }
+  uint32_t e = 0u, d = 0u;
+  for (int b = 0; b < nb; ++b) {
+    const int x = x0 + b;
+    const int8_t v = row[x];
+    e |= (uint32_t)(v == row[x + 1 == L ? 0 : x + 1]) << b;
+    d |= (uint32_t)(v == rowS[x]) << b;
+  }
+  eqE = e;
+  eqS = d;
+}
+
 // ------------------------------------------------ shared-memory union-find
 // Parents are 16-bit local site indices (par[x] <= x; roots point to
 // themselves).
@@ -531,7 +565,9 @@ struct P1Shared {
 // SPINS_GIVEN: the caller has put the spin words in S.sd[0] and the halo's
 // spins in S.bb (east column, south row), as phase 3 of the previous sweep
 // leaves them (phase31_kernel); the spins are not read from global memory.
-template <int WPR, int TH, int H, bool BATCH, bool SPINS_GIVEN = false>
+// POTTS: spins_in holds q-state Potts states (§6); an edge may bond iff its
+// two states are equal, and no spin words or halo spins are kept.
+template <int WPR, int TH, int H, bool BATCH, bool SPINS_GIVEN = false, bool POTTS = false>
 __device__ __forceinline__ void phase1_body(P1Shared<WPR, TH, H>& S, const SweepArgs& a0, const BatchArgs& bat,
                                             int T, int k) {
   using Tl = Tile<WPR, TH, H>;
@@ -564,8 +600,9 @@ __device__ __forceinline__ void phase1_body(P1Shared<WPR, TH, H>& S, const Sweep
   uint32_t* hE = s_bb + Tl::OFF_HE;
   uint32_t* hS = s_bb + Tl::OFF_HS;
 
-  if (SPINS_GIVEN) {
-    for (int i = tid; i < Tl::OFF_HE; i += NT) s_bb[i] = 0u;  // out-going bond bits; the halo is given
+  if (SPINS_GIVEN || POTTS) {
+    // out-going bond bits; the halo is given (or, for Potts, not kept)
+    for (int i = tid; i < (POTTS ? BBW : Tl::OFF_HE); i += NT) s_bb[i] = 0u;
     __syncthreads();
   } else {
     for (int i = tid; i < BBW; i += NT) s_bb[i] = 0u;
@@ -606,16 +643,28 @@ __device__ __forceinline__ void phase1_body(P1Shared<WPR, TH, H>& S, const Sweep
     const int nb = max(0, min(32, P.ncols - 32 * w));
     const uint32_t vmask = y < P.nrows ? word_mask(P.ncols, w) : 0u;
     const uint32_t lbit = last_column_bit(P.ncols, w);  // nonzero iff this word holds the tile's last column
-    const uint32_t s = s_spin[y][w];
-    uint32_t sE;
-    if (lbit) {
-      const uint32_t hb = (hE[y >> 5] >> (y & 31)) & 1u;
-      sE = ((s >> 1) & (lbit - 1u)) | (hb ? lbit : 0u);
+    uint32_t s = 0u, eqE = 0u, eqS = 0u;
+    if (POTTS) {
+      if (vmask) {
+        const int yg = P.y0 + y;
+        potts_equal_bits(a.spins_in + (size_t)yg * L, a.spins_in + (size_t)(yg + 1 == L ? 0 : yg + 1) * L,
+                         P.x0 + 32 * w, nb, L, g.aligned16, eqE, eqS);
+        eqE &= vmask;
+        eqS &= vmask;
+      }
     } else {
-      sE = (s >> 1) | ((w + 1 < WPR) ? (s_spin[y][w + 1] << 31) : 0u);
+      s = s_spin[y][w];
+      uint32_t sE;
+      if (lbit) {
+        const uint32_t hb = (hE[y >> 5] >> (y & 31)) & 1u;
+        sE = ((s >> 1) & (lbit - 1u)) | (hb ? lbit : 0u);
+      } else {
+        sE = (s >> 1) | ((w + 1 < WPR) ? (s_spin[y][w + 1] << 31) : 0u);
+      }
+      const uint32_t sS = (y + 1 < P.nrows) ? s_spin[y + 1][w] : hS[w];
+      eqE = ~(s ^ sE) & vmask;
+      eqS = ~(s ^ sS) & vmask;
     }
-    const uint32_t sS = (y + 1 < P.nrows) ? s_spin[y + 1][w] : hS[w];
-    const uint32_t eqE = ~(s ^ sE) & vmask, eqS = ~(s ^ sS) & vmask;
     uint32_t rE = 0, rS = 0;
     if (vmask) {
       const uint32_t i0 = (uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w);
@@ -963,7 +1012,7 @@ __global__ void phase2_kernel(const SweepArgs a0, const BatchArgs bat) {
 // is rewritten to name its component's root directly, together with the
 // root's key (the component's minimum site, C9) and the decision drawn
 // for it (C6, or §2.4's assignment): bits 0-31 root node, 32-62 root key,
-// 63 decision. Keys are site
+// 63 decision; for the Potts model the new state goes to nval. Keys are site
 // indices below 2^31, so bit 63 is free. Walks only read; a thread writes
 // only its own node, and the parent field it leaves (the root) is an
 // ancestor, so walks of other threads that meet a rewritten node still end
@@ -988,7 +1037,11 @@ __device__ __forceinline__ void resolve_body(const SweepArgs& a0, const BatchArg
       v = ld_node(a.tb.nodes + cur);
     }
     const uint32_t key = (uint32_t)(v >> 32) & 0x7fffffffu;
-    const uint32_t f = decision_bit(key, a.t, a.ks, a.rule);
+    uint32_t f = 0u;
+    if (a.q)
+      a.tb.nval[x] = (uint8_t)potts_new_state(key, a.t, a.ks, a.q);  // §6: the decision is a state
+    else
+      f = decision_bit(key, a.t, a.ks, a.rule);
     a.tb.nodes[x] = ((uint64_t)(key | (f << 31)) << 32) | cur;
   }
 }
@@ -1531,6 +1584,160 @@ cudaError_t launch_fused_shape(const BatchArgs& b, int ntiles, int nsweeps, cuda
   return cudaLaunchKernelEx(&cfg, kern, b, nsweeps, ntiles);
 }
 
+// ================================================================ Potts (§6)
+
+// Phase 1 of a q-state Potts sweep: the Ising phase 1 with the bond masks of
+// equal states (phase1_body's POTTS form).
+template <int WPR, int TH, int H>
+__global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
+    potts_phase1_kernel(const SweepArgs a) {
+  __shared__ P1Shared<WPR, TH, H> S;
+  phase1_body<WPR, TH, H, false, false, true>(S, a, BatchArgs{}, blockIdx.x, 0);
+}
+
+template <int WPR, int TH, int H>
+struct PottsP3Shared {
+  using T = Tile<WPR, TH, H>;
+  alignas(16) uint16_t par[TH * T::TW];  // labels from phase 1: par[par[x]] is the tile root of x
+  alignas(16) uint8_t val[TH * T::TW];   // new state of every tile root (indexed by its site)
+  alignas(16) uint8_t snew[TH][T::TW];   // new states of the tile
+  alignas(16) uint8_t hS[T::TW];         // new states of the south halo row
+  uint8_t hE[TH];                        // new states of the east halo column
+  uint8_t slotval[T::MS];                // new state of every slot's cluster (from resolve)
+  alignas(16) uint32_t bmask[T::RW];     // border roots
+  uint32_t pre[T::RW];
+  uint32_t wsum[33];
+  long long red[2][T::NT / 32];
+};
+
+// Phase 3 of a q-state Potts sweep for one tile (§6): every cluster takes the
+// state drawn for its root (a border cluster the one resolve left in its slot,
+// an inner one drawn here from its root's key), every site its cluster's, and
+// E = -(edges joining equal states), M = (sites in state 0) of the new
+// configuration are summed in int64.
+template <int WPR, int TH, int H>
+__global__ void __launch_bounds__(Tile<WPR, TH, H>::NT) potts_phase3_kernel(const SweepArgs a) {
+  using Tl = Tile<WPR, TH, H>;
+  constexpr int TW = Tl::TW, NT = Tl::NT, NB = Tl::NB, MS = Tl::MS, RW = Tl::RW;
+  constexpr int G = TW / 4;  // four-site groups per row
+  __shared__ PottsP3Shared<WPR, TH, H> S;
+  const Geometry& g = a.g;
+  const int L = g.L;
+  const TilePos P = tile_pos<TW, TH>(g, blockIdx.x);
+  const int tid = threadIdx.x, lane = tid & 31;
+
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.tb.roots + (size_t)P.tile * (TW * TH));
+    uint4* dst = reinterpret_cast<uint4*>(S.par);
+    for (int i = tid; i < TW * TH / 8; i += NT) dst[i] = src[i];
+    const uint32_t* gbm = a.tb.bmask + (size_t)P.tile * RW;
+    for (int i = tid; i < RW; i += NT) S.bmask[i] = gbm[i];
+  }
+  __syncthreads();
+  const int nsl = a.tb.nslots[P.tile];
+  if (block_popc_prefix<RW, NT>(S.bmask, S.pre, S.wsum) != nsl && tid == 0) atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+  for (int j = tid; j < nsl && j < MS; j += NT) S.slotval[j] = a.tb.nval[(size_t)P.tile * MS + j];
+  // the halo's new states: its sites are border sites of the neighbour tiles,
+  // so their clusters have slots there
+  const int tileE = P.ty * g.tiles_x + (P.tx + 1) % g.tiles_x;
+  const int tileS = ((P.ty + 1) % g.tiles_y) * g.tiles_x + P.tx;
+  for (int y = tid; y < P.nrows; y += NT) {
+    uint16_t slot = a.tb.bslot[(size_t)tileE * NB + y];
+    if (slot >= MS) {
+      atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+      slot = 0;
+    }
+    S.hE[y] = a.tb.nval[(size_t)tileE * MS + slot];
+  }
+  for (int x = tid; x < P.ncols; x += NT) {
+    uint16_t slot = a.tb.bslot[(size_t)tileS * NB + 2 * TH + x];
+    if (slot >= MS) {
+      atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+      slot = 0;
+    }
+    S.hS[x] = a.tb.nval[(size_t)tileS * MS + slot];
+  }
+  __syncthreads();
+
+  // ---- the new state of every tile root (phase 1 marked them)
+  const uint32_t* grb = a.tb.rbits + (size_t)P.tile * RW;
+  for (int rw = tid; rw < RW; rw += NT) {
+    const int y = rw / WPR, w = rw % WPR;
+    if (y >= P.nrows) continue;
+    const uint32_t bm = S.bmask[rw];
+    for (uint32_t m = grb[rw]; m; m &= m - 1) {
+      const int b = __ffs(m) - 1, x = rw * 32 + b;  // tile-local site (row-major, TW = 32 WPR)
+      uint32_t v;
+      if ((bm >> b) & 1u) {
+        const int sl = slot_of(S.bmask, S.pre, x);
+        v = sl < nsl ? S.slotval[sl] : 0u;
+      } else {
+        v = potts_new_state((uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w + b), a.t, a.ks, a.q);
+      }
+      S.val[x] = (uint8_t)v;
+    }
+  }
+  __syncthreads();
+
+  // ---- every site takes its root's state, four sites per thread and step
+  for (int i = tid; i < TH * G; i += NT) {
+    const int y = i / G, x = 4 * (i % G);
+    if (y >= P.nrows || x >= P.ncols) continue;
+    const int base = y * TW + x;
+    uint32_t word = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (x + k < P.ncols) word |= (uint32_t)S.val[S.par[S.par[base + k]]] << (8 * k);
+    *reinterpret_cast<uint32_t*>(&S.snew[y][x]) = word;
+    int8_t* out = a.spins_out + (size_t)(P.y0 + y) * L + P.x0 + x;
+    if (g.aligned16 && x + 4 <= P.ncols) {
+      *reinterpret_cast<uint32_t*>(out) = word;
+    } else {
+      for (int k = 0; k < 4 && x + k < P.ncols; ++k) out[k] = (int8_t)(word >> (8 * k));
+    }
+  }
+  __syncthreads();
+
+  // ---- E and M of the new states: east and south edge of every site
+  long long e = 0, m = 0;
+  for (int i = tid; i < TH * G; i += NT) {
+    const int y = i / G, x = 4 * (i % G);
+    if (y >= P.nrows || x >= P.ncols) continue;
+    const uint32_t cur = *reinterpret_cast<const uint32_t*>(&S.snew[y][x]);
+    if (x + 4 < P.ncols) {
+      const uint32_t nxt = *reinterpret_cast<const uint32_t*>(&S.snew[y][x + 4]);
+      const uint32_t south = y + 1 < P.nrows ? *reinterpret_cast<const uint32_t*>(&S.snew[y + 1][x])
+                                             : *reinterpret_cast<const uint32_t*>(&S.hS[x]);
+      e -= (__popc(__vcmpeq4(cur, __funnelshift_r(cur, nxt, 8))) + __popc(__vcmpeq4(cur, south))) >> 3;
+      m += __popc(__vcmpeq4(cur, 0u)) >> 3;
+    } else {
+      for (int k = 0; k < 4 && x + k < P.ncols; ++k) {
+        const uint32_t v = (cur >> (8 * k)) & 0xffu;
+        const uint32_t ve = x + k + 1 < P.ncols ? S.snew[y][x + k + 1] : S.hE[y];
+        const uint32_t vs = y + 1 < P.nrows ? S.snew[y + 1][x + k] : S.hS[x + k];
+        e -= (v == ve) + (v == vs);
+        m += v == 0u;
+      }
+    }
+  }
+  e = warp_sum(e);
+  m = warp_sum(m);
+  if (lane == 0) {
+    S.red[0][tid >> 5] = e;
+    S.red[1][tid >> 5] = m;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    long long et = 0, mt = 0;
+    for (int k = 0; k < NT / 32; ++k) {
+      et += S.red[0][k];
+      mt += S.red[1][k];
+    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(a.em), (unsigned long long)et);
+    atomicAdd(reinterpret_cast<unsigned long long*>(a.em + 1), (unsigned long long)mt);
+  }
+}
+
 // ================================================================ helpers
 
 __global__ void init_kernel(int8_t* spins, long long n, KeySchedule ks, int cold) {
@@ -1676,6 +1883,19 @@ cudaError_t launch_phase3(int shape, const SweepArgs& a, bool labels_mode, cudaS
 cudaError_t launch_phase4(int shape, const SweepArgs& a, cudaStream_t st) { return dispatch(shape, 4, a, 0, nullptr, st); }
 cudaError_t launch_export_bonds(int shape, const SweepArgs& a, uint8_t* out, cudaStream_t st) {
   return dispatch(shape, 5, a, 0, out, st);
+}
+
+cudaError_t launch_potts_phase1(const SweepArgs& a, cudaStream_t st) {
+  constexpr TileShape ts = shape_of(kPottsShape);
+  potts_phase1_kernel<ts.wpr, ts.th, ts.h><<<a.g.tiles_x * a.g.tiles_y, 32 * ts.wpr, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_potts_phase3(const SweepArgs& a, cudaStream_t st) {
+  constexpr TileShape ts = shape_of(kPottsShape);
+  potts_phase3_kernel<ts.wpr, ts.th, ts.h>
+      <<<a.g.tiles_x * a.g.tiles_y, Tile<ts.wpr, ts.th, ts.h>::NT, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batch_phase(int shape, int which, const BatchArgs& b, int ntiles, cudaStream_t st) {

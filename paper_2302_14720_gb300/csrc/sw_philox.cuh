@@ -86,4 +86,11 @@ __device__ __forceinline__ uint32_t decision_bit(uint32_t root, uint32_t t, cons
   return rule ? assign_bit(root, t, ks) : flip_bit(root, t, ks);
 }
 
+// §6 (q-state Potts): the cluster rooted at `root` takes state
+// floor(x0 q / 2^32) in sweep t, x0 the first word of block (root, t, 3, 0);
+// for q = 2 this is the assignment rule's sign bit.
+__device__ __forceinline__ uint32_t potts_new_state(uint32_t root, uint32_t t, const KeySchedule& ks, uint32_t q) {
+  return (uint32_t)(((uint64_t)philox4x32_10(make_uint4(root, t, 3u, 0u), ks).x * q) >> 32);
+}
+
 }  // namespace sw

@@ -2,18 +2,19 @@
 // paper's §6 generalisation), H = -sum over the 2N edges of
 // delta(s_i, s_j), states 0..q-1 as int8.
 //
-// One sweep is four site-parallel kernels over global memory:
-//   bonds   a thread per Philox block (site pair, C5 counters): an edge bonds
-//           iff its two states are equal and its word < thr, thr from
-//           p = 1 - exp(-beta); every site starts as its own root;
-//   unite   a thread per site unites the two ends of its east and south
-//           bonds (lock-free union-find over int32 parents, the larger root
-//           hung under the smaller with atomicMin, path halving), so every
-//           root ends as its cluster's smallest site (C9);
-//   roots   every site points at its root; each root draws its cluster's
-//           new state floor(x0 q / 2^32) from block (root, t, 3, 0);
-//   assign  every site takes its root's state; E = -(edges joining equal
-//           states) and M = (sites in state 0) are reduced in int64.
+// A sweep runs on the tiled path of the Ising sweep (tile shape
+// kPottsShape, 128 x 64 sites):
+//   phase 1  bonds and tile clusters: an edge bonds iff its two states are
+//            equal and its word of the site pair's Philox block (C5) is
+//            below thr, thr from p = 1 - exp(-beta); then the band-scan
+//            tile labelling, border slots and global nodes of the Ising
+//            phase 1 (the bond masks are all it looks at);
+//   phase 2  the cross-tile merge, and the resolve pass that draws each
+//            border cluster's new state floor(x0 q / 2^32), x0 from block
+//            (root, t, 3, 0), root its smallest site (C9);
+//   phase 3  inner clusters draw their state the same way, every site takes
+//            its cluster's, and E = -(edges joining equal states),
+//            M = (sites in state 0) are reduced in int64.
 // For q = 2 and twice the Ising coupling this is the Ising sweep with the
 // assignment rule (C6b), state 1 <-> spin -1.
 #include <cuda_runtime.h>
@@ -29,45 +30,12 @@
 
 namespace {
 
-constexpr int kPottsFindCap = 1 << 24;
-constexpr int kPottsUnionCap = 1 << 16;
-
 __device__ __forceinline__ int8_t potts_state(uint32_t x, int q) {
   return (int8_t)(((uint64_t)x * (uint64_t)q) >> 32);
 }
 
-__device__ __forceinline__ int pfind(int* par, int x, int* err) {
-  for (int it = 0;; ++it) {
-    const int p = __ldcg(par + x);
-    if (p == x) return x;
-    const int gp = __ldcg(par + p);
-    if (gp == p) return p;
-    if (it >= kPottsFindCap) {
-      atomicCAS(err, 0, 1);
-      return p;
-    }
-    atomicMin(par + x, gp);  // halving: x now points at an ancestor
-    x = gp;
-  }
-}
-
-__device__ void punite(int* par, int a, int b, int* err) {
-  for (int it = 0; it < kPottsUnionCap; ++it) {
-    a = pfind(par, a, err);
-    b = pfind(par, b, err);
-    if (a == b) return;
-    if (a < b) {
-      const int t = a;
-      a = b;
-      b = t;
-    }
-    const int old = atomicMin(par + a, b);
-    if (old == a) return;
-    a = old;
-  }
-  atomicCAS(err, 0, 1);
-}
-
+// C7 for Potts: site i starts in state floor(x0 q / 2^32), x0 the first word
+// of block (i, 0, 2, 0) (hot), or in state 0 (cold).
 __global__ void potts_init_kernel(int8_t* s, int64_t n, int q, sw::KeySchedule ks, int cold) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     s[i] = cold ? (int8_t)0 : potts_state(sw::philox4x32_10(make_uint4((uint32_t)i, 0u, 2u, 0u), ks).x, q);
@@ -75,92 +43,7 @@ __global__ void potts_init_kernel(int8_t* s, int64_t n, int q, sw::KeySchedule k
 
 __global__ void potts_check_kernel(const int8_t* s, int64_t n, int q, int* err) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (s[i] < 0 || s[i] >= q) atomicCAS(err, 0, 2);
-}
-
-__global__ void potts_bonds_kernel(const int8_t* s, uint8_t* bonds, int* par, int L, uint32_t thr, uint32_t t,
-                                   sw::KeySchedule ks, int64_t* em) {
-  const int64_t n = (int64_t)L * L;
-  const int64_t npairs = (n + 1) / 2;
-  if (blockIdx.x == 0 && threadIdx.x < 2) em[threadIdx.x] = 0;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 w = sw::philox4x32_10(make_uint4((uint32_t)p, t, 0u, 0u), ks);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int64_t i = 2 * p + j;
-      if (i >= n) break;
-      const int y = (int)(i / L), x = (int)(i - (int64_t)y * L);
-      const int8_t si = s[i];
-      const int8_t se = s[(int64_t)y * L + (x + 1 == L ? 0 : x + 1)];
-      const int8_t ss = s[(int64_t)(y + 1 == L ? 0 : y + 1) * L + x];
-      const uint32_t ue = j ? w.z : w.x, us = j ? w.w : w.y;
-      bonds[i] = (uint8_t)((si == se && ue < thr ? 1u : 0u) | (si == ss && us < thr ? 2u : 0u));
-      par[i] = (int)i;
-    }
-  }
-}
-
-__global__ void potts_unite_kernel(const uint8_t* bonds, int* par, int L, int* err) {
-  const int64_t n = (int64_t)L * L;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint8_t b = bonds[i];
-    if (!b) continue;
-    const int y = (int)(i / L), x = (int)(i - (int64_t)y * L);
-    if (b & 1u) punite(par, (int)i, (int)((int64_t)y * L + (x + 1 == L ? 0 : x + 1)), err);
-    if (b & 2u) punite(par, (int)i, (int)((int64_t)(y + 1 == L ? 0 : y + 1) * L + x), err);
-  }
-}
-
-__global__ void potts_roots_kernel(int* par, int8_t* val, int64_t n, int q, uint32_t t, sw::KeySchedule ks,
-                                   int* err) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int r = (int)i, p = __ldcg(par + r);
-    for (int it = 0; p != r; ++it) {
-      if (it >= kPottsFindCap) {
-        atomicCAS(err, 0, 1);
-        break;
-      }
-      r = p;
-      p = __ldcg(par + r);
-    }
-    par[i] = r;  // concurrent stores all write roots
-    if (r == (int)i) val[i] = potts_state(sw::philox4x32_10(make_uint4((uint32_t)i, t, 3u, 0u), ks).x, q);
-  }
-}
-
-__global__ void potts_assign_kernel(int8_t* s, const int* par, const int8_t* val, int L, int64_t* em) {
-  const int64_t n = (int64_t)L * L;
-  long long e = 0, m = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int y = (int)(i / L), x = (int)(i - (int64_t)y * L);
-    const int8_t v = val[par[i]];
-    const int8_t ve = val[par[(int64_t)y * L + (x + 1 == L ? 0 : x + 1)]];
-    const int8_t vs = val[par[(int64_t)(y + 1 == L ? 0 : y + 1) * L + x]];
-    s[i] = v;
-    e -= (v == ve) + (v == vs);
-    m += v == 0;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    e += __shfl_xor_sync(0xffffffffu, e, o);
-    m += __shfl_xor_sync(0xffffffffu, m, o);
-  }
-  __shared__ long long red[2][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][warp] = e;
-    red[1][warp] = m;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long et = 0, mt = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-      et += red[0][k];
-      mt += red[1][k];
-    }
-    atomicAdd(reinterpret_cast<unsigned long long*>(em), (unsigned long long)et);
-    atomicAdd(reinterpret_cast<unsigned long long*>(em + 1), (unsigned long long)mt);
-  }
+    if (s[i] < 0 || s[i] >= q) atomicCAS(err, 0, sw::kErrBadSpin);
 }
 
 int grid_of(int64_t n) {
@@ -182,12 +65,12 @@ struct sw_potts {
   int64_t t = 0, t_base = 0, cap = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  int8_t* s = nullptr;
-  uint8_t* bonds = nullptr;
-  int* par = nullptr;
-  int8_t* val = nullptr;
-  int64_t* em = nullptr;
-  int* err = nullptr;
+  sw::Geometry g{};
+  sw::TileBuffers tb{};
+  int8_t* s = nullptr;        // states [L][L]
+  int8_t* staging = nullptr;  // sw_potts_set_state's checked copy
+  int32_t* label_buf = nullptr;
+  int64_t* em = nullptr;      // [cap][2]
 };
 
 namespace {
@@ -202,20 +85,30 @@ namespace {
   } while (0)
 
 void free_potts(sw_potts* h) {
-  void* ptrs[] = {h->s, h->bonds, h->par, h->val, h->em, h->err};
+  void* ptrs[] = {h->s,         h->staging,   h->label_buf,  h->em,       h->tb.tbits, h->tb.roots,
+                  h->tb.bmask,  h->tb.rbits,  h->tb.nodes,   h->tb.bslot, h->tb.bbits, h->tb.nslots,
+                  h->tb.err,    h->tb.nval};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
+// Synchronise and turn the device error flag into a status.
 int check_potts(sw_potts* h) {
   P_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
   int flag = 0;
-  P_CUDA(cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost), "error flag read");
-  if (flag == 1) return pfail(SW_ETIMEOUT, "a capped union-find loop gave up");
-  if (flag == 2) return pfail(SW_EINVAL, "a state outside 0..q-1 was given");
-  if (flag != 0) return pfail(SW_EDEVICE, "device error flag set");
-  return SW_OK;
+  P_CUDA(cudaMemcpy(&flag, h->tb.err, sizeof(int), cudaMemcpyDeviceToHost), "error flag read");
+  switch (flag) {
+    case sw::kErrNone: return SW_OK;
+    case sw::kErrUnionCap: return pfail(SW_ETIMEOUT, "a capped union-find loop gave up");
+    case sw::kErrBadSpin:
+      // the state was not replaced: report once
+      P_CUDA(cudaMemset(h->tb.err, 0, sizeof(int)), "error flag reset");
+      return pfail(SW_EINVAL, "a state outside 0..q-1 was given");
+    case sw::kErrSlotOverflow: return pfail(SW_EDEVICE, "device: tile border slots overflowed");
+    case sw::kErrCopyTimeout: return pfail(SW_ETIMEOUT, "device: a bulk copy into shared memory did not complete");
+    default: return pfail(SW_EDEVICE, "device error flag set");
+  }
 }
 
 int grow(sw_potts* h, int64_t need) {
@@ -245,15 +138,25 @@ uint32_t potts_thr(double beta) {
   return (uint32_t)scaled;
 }
 
-// Bonds of the current states and counter, clusters to roots.
-int clusters(sw_potts* h) {
-  const int64_t n = (int64_t)h->L * h->L;
-  const uint32_t t = (uint32_t)h->t;
-  int64_t* em = h->em + 2 * (h->t - h->t_base);
-  potts_bonds_kernel<<<grid_of((n + 1) / 2), 256, 0, h->stream>>>(h->s, h->bonds, h->par, h->L, h->thr, t, h->ks, em);
-  potts_unite_kernel<<<grid_of(n), 256, 0, h->stream>>>(h->bonds, h->par, h->L, h->err);
-  potts_roots_kernel<<<grid_of(n), 256, 0, h->stream>>>(h->par, h->val, n, h->q, t, h->ks, h->err);
-  P_CUDA(cudaGetLastError(), "Potts sweep launch");
+sw::SweepArgs args_of(const sw_potts* h) {
+  sw::SweepArgs a{};
+  a.g = h->g;
+  a.thr = h->thr;
+  a.t = (uint32_t)h->t;
+  a.rule = SW_RULE_ASSIGN;
+  a.q = (uint32_t)h->q;
+  a.ks = h->ks;
+  a.tb = h->tb;
+  a.spins_in = h->s;
+  a.spins_out = h->s;
+  return a;
+}
+
+// Phases 1-2 of the current states and counter: bonds, tile clusters, the
+// merge and each border cluster's new state.
+int clusters(sw_potts* h, const sw::SweepArgs& a) {
+  P_CUDA(sw::launch_potts_phase1(a, h->stream), "Potts phase 1 launch");
+  P_CUDA(sw::launch_phase2(sw::kPottsShape, a, h->stream), "Potts phase 2 launch");
   return SW_OK;
 }
 
@@ -284,6 +187,12 @@ int sw_potts_create(int32_t L, int32_t q, double beta, uint64_t seed, int32_t in
   h->q = q;
   h->thr = potts_thr(beta);
   h->ks = sw::make_key_schedule(seed);
+  const sw::TileShape ts = sw::shape_of(sw::kPottsShape);
+  h->g.L = L;
+  h->g.tiles_x = (L + ts.tw() - 1) / ts.tw();
+  h->g.tiles_y = (L + ts.th - 1) / ts.th;
+  h->g.aligned16 = (L % 16) == 0;
+  const size_t ntiles = (size_t)h->g.tiles_x * h->g.tiles_y;
   const size_t n = (size_t)L * L;
   cudaError_t e = cudaSuccess;
   if (stream) {
@@ -293,11 +202,17 @@ int sw_potts_create(int32_t L, int32_t q, double beta, uint64_t seed, int32_t in
     h->own_stream = e == cudaSuccess;
   }
   if (e == cudaSuccess) e = cudaMalloc(&h->s, n);
-  if (e == cudaSuccess) e = cudaMalloc(&h->bonds, n);
-  if (e == cudaSuccess) e = cudaMalloc(&h->par, n * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&h->val, n);
-  if (e == cudaSuccess) e = cudaMalloc(&h->err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.tbits, ntiles * 3 * ts.row_words() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.roots, ntiles * ts.sites() * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.bmask, ntiles * ts.row_words() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.rbits, ntiles * ts.row_words() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.nodes, ntiles * ts.max_slots() * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.bslot, ntiles * ts.boundary_sites() * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.bbits, ntiles * ts.bbits_words() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.nslots, ntiles * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.nval, ntiles * ts.max_slots());
+  if (e == cudaSuccess) e = cudaMalloc(&h->tb.err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->tb.err, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) {
     potts_init_kernel<<<grid_of((int64_t)n), 256, 0, h->stream>>>(h->s, (int64_t)n, q, h->ks, init == SW_INIT_COLD);
     e = cudaGetLastError();
@@ -323,13 +238,12 @@ int sw_potts_sweep(sw_potts* h, int32_t n) {
   if (n < 0) return pfail(SW_EINVAL, "n must be >= 0");
   int rc = grow(h, h->t - h->t_base + n);
   if (rc != SW_OK) return rc;
-  const int64_t N = (int64_t)h->L * h->L;
   for (int32_t k = 0; k < n; ++k) {
-    rc = clusters(h);
+    sw::SweepArgs a = args_of(h);
+    a.em = h->em + 2 * (h->t - h->t_base);  // zeroed by phase 1
+    rc = clusters(h, a);
     if (rc != SW_OK) return rc;
-    int64_t* em = h->em + 2 * (h->t - h->t_base);
-    potts_assign_kernel<<<grid_of(N), 256, 0, h->stream>>>(h->s, h->par, h->val, h->L, em);
-    P_CUDA(cudaGetLastError(), "Potts assign launch");
+    P_CUDA(sw::launch_potts_phase3(a, h->stream), "Potts phase 3 launch");
     h->t += 1;
   }
   return SW_OK;
@@ -370,19 +284,16 @@ int sw_potts_set_state(sw_potts* h, const int8_t* states, uint32_t t, int32_t in
   const size_t n = (size_t)h->L * h->L;
   int rc = check_potts(h);
   if (rc != SW_OK) return rc;
-  // staged in the per-sweep value buffer and checked before it replaces the state
-  P_CUDA(cudaMemcpyAsync(h->val, states, n, in_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+  if (!h->staging) P_CUDA(cudaMalloc(&h->staging, n), "staging buffer");
+  // checked in the staging buffer before it replaces the state
+  P_CUDA(cudaMemcpyAsync(h->staging, states, n, in_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          h->stream),
          "states copy");
-  potts_check_kernel<<<grid_of((int64_t)n), 256, 0, h->stream>>>(h->val, (int64_t)n, h->q, h->err);
+  potts_check_kernel<<<grid_of((int64_t)n), 256, 0, h->stream>>>(h->staging, (int64_t)n, h->q, h->tb.err);
   P_CUDA(cudaGetLastError(), "state check launch");
   rc = check_potts(h);
-  if (rc != SW_OK) {
-    cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
-    cudaStreamSynchronize(h->stream);
-    return rc;
-  }
-  P_CUDA(cudaMemcpyAsync(h->s, h->val, n, cudaMemcpyDeviceToDevice, h->stream), "states copy");
+  if (rc != SW_OK) return rc;
+  P_CUDA(cudaMemcpyAsync(h->s, h->staging, n, cudaMemcpyDeviceToDevice, h->stream), "states copy");
   h->t = t;
   h->t_base = t;
   return SW_OK;
@@ -390,15 +301,19 @@ int sw_potts_set_state(sw_potts* h, const int8_t* states, uint32_t t, int32_t in
 
 int sw_potts_labels(sw_potts* h, int32_t* out, int32_t out_is_device) {
   if (!h || !out) return pfail(SW_EINVAL, "NULL argument");
-  int rc = grow(h, h->t - h->t_base + 1);  // the bonds kernel zeroes the next trace row
-  if (rc != SW_OK) return rc;
-  rc = clusters(h);
-  if (rc != SW_OK) return rc;
   const size_t n = (size_t)h->L * h->L;
-  P_CUDA(cudaMemcpyAsync(out, h->par, n * sizeof(int32_t),
-                         out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream),
-         "labels copy");
+  int32_t* dst = out;
+  if (!out_is_device) {
+    if (!h->label_buf) P_CUDA(cudaMalloc(&h->label_buf, n * sizeof(int32_t)), "label buffer");
+    dst = h->label_buf;
+  }
+  sw::SweepArgs a = args_of(h);
+  int rc = clusters(h, a);
+  if (rc != SW_OK) return rc;
+  a.labels = dst;
+  P_CUDA(sw::launch_phase3(sw::kPottsShape, a, true, h->stream), "labels launch");
   if (out_is_device) return SW_OK;
+  P_CUDA(cudaMemcpyAsync(out, dst, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "labels copy");
   return check_potts(h);
 }
 

@@ -1,6 +1,9 @@
-"""q-state Potts sweeps on the GPU (the paper's §6 generalisation): chains
-bit-exact against the oracle's Potts chain, labels against the oracle's BFS
-labels of the same bonds, q = 2 against the Ising assignment chain."""
+"""q-state Potts sweeps on the GPU (the paper's §6 generalisation), on the
+tiled path (128 x 64 tiles): chains bit-exact against the oracle's Potts
+chain -- one tile, ragged tiles, many tiles with rows on and off 16-byte
+boundaries, clusters spanning the lattice (large beta), q up to 127 --
+labels against the oracle's labels of the same bonds, q = 2 against the
+Ising assignment chain."""
 import numpy as np
 import pytest
 
@@ -20,7 +23,9 @@ def sw():
 
 @pytest.mark.parametrize("L,q,beta,cold", [(2, 3, 0.7, False), (5, 4, 1.2, True), (33, 3, 1.0050833, False),
                                            (64, 2, 0.88137, False), (100, 5, 1.1, False), (257, 3, 1.3, False),
-                                           (130, 10, 1.4, True)])
+                                           (130, 10, 1.4, True), (512, 3, 1.0050833, False),
+                                           (1000, 3, 1.0050833, False), (256, 4, 4.0, False),
+                                           (200, 127, 2.0, False), (129, 2, 0.1, False)])
 def test_potts_chain_parity(sw, L, q, beta, cold):
     seed, n = 600 + L + q, 7
     with sw.Potts(L, q, beta, seed, sw.SW_INIT_COLD if cold else sw.SW_INIT_HOT) as p:
