@@ -215,9 +215,9 @@ int sw_bonds(sw_lattice* h, uint8_t* out_host);
  * stream (accumulators cleared); enable = 0 stops recording. Phases:
  * 0 = bonds + tile-local clusters, 1 = cross-tile merge, 2 = flips + E/M,
  * 3 = cluster statistics, 4 = flips + E/M of a sweep together with the bonds
- * and tile-local clusters of the next sweep (the one launch sw_sweep uses
- * for both when statistics are off; a call whose previous call ended with
- * it starts at phase 1). Not part of the paper: measurement support. */
+ * and tile-local clusters of the next sweep of the same call (one launch,
+ * on the 128x64 and 128x128 tile shapes with statistics off; a call's last
+ * sweep runs phase 2 alone). Not part of the paper: measurement support. */
 #define SW_TIMING_PHASES 5
 int sw_timing(sw_lattice* h, int32_t enable);
 

@@ -111,7 +111,6 @@ struct sw_lattice {
   int32_t* nslots2 = nullptr;
   uint64_t* nodes2 = nullptr;
   bool fuse = false;       // the tile shape has the phase31 launch
-  bool p1_ready = false;   // phase 1 of sweep t (the current counter) has run on the current spins
   int8_t* spins = nullptr;
   uint32_t* csize = nullptr;
   int64_t* em = nullptr;    // [cap][2]
@@ -265,7 +264,6 @@ int range_ok(const sw_lattice* h, int64_t first, int64_t count) {
 
 // Phases 1-2 for the current state and counter (bonds, tile clusters, merge).
 int run_clusters(sw_lattice* h, sw::SweepArgs& a) {
-  h->p1_ready = false;  // phase 2 below changes the nodes a carried-over phase 1 left
   a.em = nullptr;
   a.hist = nullptr;
   a.csize = nullptr;
@@ -368,8 +366,7 @@ int sw_sweep(sw_lattice* h, int32_t n) {
   if (!h) return fail(SW_EINVAL, "handle is NULL");
   if (n < 0) return fail(SW_EINVAL, "n must be >= 0");
   if (n == 0) return SW_OK;
-  // one row more: a carried-over phase 1 zeroes the next sweep's row
-  int rc = ensure_trace(h, h->t - h->t_base + n + 1);
+  int rc = ensure_trace(h, h->t - h->t_base + n);
   if (rc != SW_OK) return rc;
   const sw::TileShape ts = sw::shape_of(h->shape);
   (void)ts;
@@ -386,36 +383,34 @@ int sw_sweep(sw_lattice* h, int32_t n) {
     s.em = h->em + 2 * (h->t - h->t_base);
     s.err = h->tb.err;
     SW_CUDA(timed_phase(h, 0, [&] { return sw::launch_small(s, h->stream); }), "small-lattice sweep launch");
-    h->p1_ready = false;
     h->t += n;
     return SW_OK;
   }
   // Without statistics and on a shape that has it, phase 3 of a sweep and
-  // phase 1 of the next one run as one launch (phase31), including after the
-  // call's last sweep: the next call then starts at phase 2. Every state
-  // change (sw_set_state*, sw_histogram, a call that runs phase 1 itself)
-  // drops that carried-over phase 1.
+  // phase 1 of the next sweep of this call run as one launch (phase31); the
+  // call's last sweep runs phase 3 alone, so no work is carried from one
+  // call to the next (the caller may change the state in between).
   const bool fused = h->fuse && !h->hist_on;
-  if (!fused && h->p1_ready) h->p1_ready = false;
+  bool carried = false;  // phase 1 of the current sweep ran in the previous launch
   for (int32_t k = 0; k < n; ++k) {
     sw::SweepArgs a = args_of(h);
     const int64_t row = h->t - h->t_base;
     a.em = h->em + 2 * row;
     a.hist = h->hist + SW_HIST_WORDS * row;
     a.csize = h->hist_on ? h->csize : nullptr;
-    if (!h->p1_ready)
+    if (!carried)
       SW_CUDA(timed_phase(h, 0, [&] { return sw::launch_phase1(h->shape, a, h->stream); }), "phase 1 launch");
-    h->p1_ready = false;
+    carried = false;
     SW_CUDA(timed_phase(h, 1, [&] { return sw::launch_phase2(h->shape, a, h->stream); }), "phase 2 launch");
     if (!h->hist_on) a.hist = nullptr;
-    if (fused) {
+    if (fused && k + 1 < n) {
       sw::SweepArgs a1 = args_of(h, h->t + 1);
-      a1.em = h->em + 2 * (row + 1);  // zeroed by the next sweep's phase 1 (the trace has room)
+      a1.em = h->em + 2 * (row + 1);  // zeroed by the next sweep's phase 1
       a1.hist = nullptr;
       a1.csize = nullptr;
       SW_CUDA(timed_phase(h, 4, [&] { return sw::launch_phase31(h->shape, a, a1, h->stream); }),
               "phase 3 + next phase 1 launch");
-      h->p1_ready = true;
+      carried = true;
     } else {
       SW_CUDA(timed_phase(h, 2, [&] { return sw::launch_phase3(h->shape, a, false, h->stream); }), "phase 3 launch");
       if (h->hist_on)
@@ -464,7 +459,6 @@ int sw_set_rule(sw_lattice* h, int32_t rule) {
 
 int sw_histogram(sw_lattice* h, int32_t enable) {
   if (!h) return fail(SW_EINVAL, "handle is NULL");
-  if (h->hist_on != (enable != 0)) h->p1_ready = false;  // phase 1 zeroes the size counters with statistics on
   h->hist_on = enable != 0;
   return SW_OK;
 }
@@ -551,7 +545,6 @@ int sw_set_state_async(sw_lattice* h, const int8_t* spins, uint32_t t) {
   SW_CUDA(cudaGetLastError(), "restore launch");
   h->t = t;
   h->t_base = t;
-  h->p1_ready = false;
   return SW_OK;
 }
 
@@ -579,7 +572,6 @@ int sw_set_state(sw_lattice* h, const int8_t* spins, uint32_t t, int32_t in_is_d
   }
   h->t = t;
   h->t_base = t;
-  h->p1_ready = false;
   return SW_OK;
 }
 
@@ -643,7 +635,6 @@ int sw_labels_equivalence(sw_lattice* h, int32_t* out, int32_t out_is_device, in
   a.em = nullptr;
   a.hist = nullptr;
   a.csize = nullptr;
-  h->p1_ready = false;
   SW_CUDA(sw::launch_phase1(h->shape, a, h->stream), "phase 1 launch");
   SW_CUDA(sw::launch_export_bonds(h->shape, a, h->bond_buf, h->stream), "bond export launch");
   int its = 0;

@@ -486,8 +486,6 @@ __device__ __forceinline__ int slot_of(const uint32_t* bmask, const uint32_t* pr
   return (int)(pre[r >> 5] + (uint32_t)__popc(bmask[r >> 5] & ((1u << (r & 31)) - 1u)));
 }
 
-// The sweep arguments of this CTA's tile: the kernel parameter for one
-// lattice, or the replica descriptor of the batch tile blockIdx.x.
 // The sweep arguments of a tile: the kernel parameter for one lattice (tile
 // T), or the replica descriptor of batch tile T. k: sweeps past the
 // descriptor's counter (the fused batch kernel runs several sweeps in one
@@ -553,13 +551,19 @@ struct P1Shared {
   using T = Tile<WPR, TH, H>;
   alignas(16) uint16_t par[TH * T::TW];  // label of every site; a label's entry is its union-find parent
   // spin bits and south bonds of the row words; once the row masks are
-  // built, the warps' union work lists, then the border-root marks
+  // built, the warps' union work lists; after the unions, sd[0] holds the
+  // border-root marks and sd[1] the border sites' roots (int16)
   alignas(16) uint32_t sd[2][TH][WPR];
-  uint32_t eint[TH][WPR];
+  union {
+    uint32_t eint[TH][WPR];  // east bonds inside the tile (to the cross-band unions)
+    uint32_t pre[T::RW];     // then the prefix counts of the border-root marks
+  };
   uint32_t bb[T::BBW];
-  int16_t broot[T::NB];
-  uint32_t pre[T::RW];  // prefix counts of the border-root marks
   uint32_t wsum[33];
+  // the border sites' roots live in sd[1] where they fit (TH >= 64), else here
+  static constexpr bool kOwnBroot = T::NB * sizeof(int16_t) > sizeof(uint32_t) * TH * WPR;
+  int16_t broot_own[kOwnBroot ? T::NB : 1];
+  __device__ int16_t* broot() { return kOwnBroot ? broot_own : reinterpret_cast<int16_t*>(&sd[1][0][0]); }
 };
 
 // SPINS_GIVEN: the caller has put the spin words in S.sd[0] and the halo's
@@ -579,7 +583,7 @@ __device__ __forceinline__ void phase1_body(P1Shared<WPR, TH, H>& S, const Sweep
   uint32_t(&s_sd)[2][TH][WPR] = S.sd;
   uint32_t(&s_eint)[TH][WPR] = S.eint;
   uint32_t* const s_bb = S.bb;
-  int16_t* const s_broot = S.broot;
+  int16_t* const s_broot = S.broot();  // written after the unions
   uint32_t* const s_pre = S.pre;
   uint32_t* const s_wsum = S.wsum;
   uint32_t(*const s_spin)[WPR] = s_sd[0];
@@ -942,8 +946,16 @@ __device__ __forceinline__ void phase1_body(P1Shared<WPR, TH, H>& S, const Sweep
   }
 }
 
+// The stand-alone phase 1 asks for eleven CTAs an SM (at most 40 registers a
+// thread, 8 bytes spilled; its 19.6 KB of shared memory fit eleven times):
+// 1.1 % faster than ten at L = 8192.
+template <int NT>
+constexpr int phase1_min_blocks() {
+  return 1408 / NT > 0 ? 1408 / NT : 1;
+}
+
 template <int WPR, int TH, int H, bool BATCH>
-__global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
+__global__ void __launch_bounds__(32 * WPR, phase1_min_blocks<32 * WPR>())
     phase1_kernel(const SweepArgs a0, const BatchArgs bat) {
   __shared__ P1Shared<WPR, TH, H> S;
   phase1_body<WPR, TH, H, BATCH>(S, a0, bat, blockIdx.x, 0);
@@ -951,53 +963,61 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
 
 // ================================================================ phase 2
 
+// Out-going border edge e of a tile (e < TH: the east edge of row e; else
+// the south edge of column e - TH): true, with the two slot nodes to unite,
+// iff the edge is bonded and does not repeat the previous edge's slot pair.
+template <int WPR, int TH, int H>
+__device__ __forceinline__ bool border_union(const SweepArgs& a, const TilePos& P, int tile, int e, uint32_t& na,
+                                             uint32_t& nb) {
+  using Tl = Tile<WPR, TH, H>;
+  constexpr int TW = Tl::TW, NB = Tl::NB, MS = Tl::MS, BBW = Tl::BBW;
+  const Geometry& g = a.g;
+  const uint32_t* bb = a.tb.bbits + (size_t)tile * BBW;
+  const uint16_t* bs = a.tb.bslot + (size_t)tile * NB;
+  int i, off_out, off_a, off_b, nbr;
+  if (e < TH) {
+    i = e;
+    if (i >= P.nrows) return false;
+    off_out = Tl::OFF_EOUT;
+    off_a = TH;  // my right column
+    off_b = 0;   // the east tile's left column
+    nbr = P.ty * g.tiles_x + (P.tx + 1) % g.tiles_x;
+  } else {
+    i = e - TH;
+    if (i >= P.ncols) return false;
+    off_out = Tl::OFF_SOUT;
+    off_a = 2 * TH + TW;  // my bottom row
+    off_b = 2 * TH;       // the south tile's top row
+    nbr = ((P.ty + 1) % g.tiles_y) * g.tiles_x + P.tx;
+  }
+  const uint32_t* out = bb + off_out;
+  if (!((out[i >> 5] >> (i & 31)) & 1u)) return false;
+  const uint16_t* bsN = a.tb.bslot + (size_t)nbr * NB;
+  const uint16_t sa = __ldcg(bs + off_a + i), sb = __ldcg(bsN + off_b + i);
+  if (sa >= __ldcg(a.tb.nslots + tile) || sb >= __ldcg(a.tb.nslots + nbr)) {
+    atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+    return false;
+  }
+  if (i > 0 && ((out[(i - 1) >> 5] >> ((i - 1) & 31)) & 1u) && __ldcg(bs + off_a + i - 1) == sa &&
+      __ldcg(bsN + off_b + i - 1) == sb)
+    return false;
+  na = (uint32_t)tile * MS + sa;
+  nb = (uint32_t)nbr * MS + sb;
+  return true;
+}
+
 // Per tile, every out-going border edge: TH east edges (rows) then TW south
 // edges (columns), one edge per thread at a time.
 template <int WPR, int TH, int H, bool BATCH>
 __device__ __forceinline__ void phase2_body(const SweepArgs& a0, const BatchArgs& bat, int T, int k) {
   using Tl = Tile<WPR, TH, H>;
-  constexpr int TW = Tl::TW, NB = Tl::NB, MS = Tl::MS, BBW = Tl::BBW;
   SweepArgs a;
   int tile;
   if (!cta_args<BATCH>(a0, bat, T, k, a, tile)) return;
-  const Geometry& g = a.g;
-  const TilePos P = tile_pos<TW, TH>(g, tile);
-  const uint32_t* bb = a.tb.bbits + (size_t)tile * BBW;
-  const uint16_t* bs = a.tb.bslot + (size_t)tile * NB;
-  for (int e = threadIdx.x; e < TH + TW; e += blockDim.x) {
-    if (e < TH) {
-      const int y = e;
-      if (y >= P.nrows) continue;
-      const uint32_t* eo = bb + Tl::OFF_EOUT;
-      if (!((eo[y >> 5] >> (y & 31)) & 1u)) continue;
-      const int tileE = P.ty * g.tiles_x + (P.tx + 1) % g.tiles_x;
-      const uint16_t* bsE = a.tb.bslot + (size_t)tileE * NB;
-      const uint16_t sa = __ldcg(bs + TH + y), sb = __ldcg(bsE + y);
-      if (sa >= __ldcg(a.tb.nslots + tile) || sb >= __ldcg(a.tb.nslots + tileE)) {
-        atomicCAS(a.tb.err, 0, kErrSlotOverflow);
-        continue;
-      }
-      if (y > 0 && ((eo[(y - 1) >> 5] >> ((y - 1) & 31)) & 1u) && __ldcg(bs + TH + y - 1) == sa &&
-          __ldcg(bsE + y - 1) == sb)
-        continue;
-      unite_global(a.tb.nodes, (uint32_t)tile * MS + sa, (uint32_t)tileE * MS + sb, a.tb.err);
-    } else {
-      const int x = e - TH;
-      if (x >= P.ncols) continue;
-      const uint32_t* so = bb + Tl::OFF_SOUT;
-      if (!((so[x >> 5] >> (x & 31)) & 1u)) continue;
-      const int tileS = ((P.ty + 1) % g.tiles_y) * g.tiles_x + P.tx;
-      const uint16_t* bsS = a.tb.bslot + (size_t)tileS * NB;
-      const uint16_t sa = __ldcg(bs + 2 * TH + TW + x), sb = __ldcg(bsS + 2 * TH + x);
-      if (sa >= __ldcg(a.tb.nslots + tile) || sb >= __ldcg(a.tb.nslots + tileS)) {
-        atomicCAS(a.tb.err, 0, kErrSlotOverflow);
-        continue;
-      }
-      if (x > 0 && ((so[(x - 1) >> 5] >> ((x - 1) & 31)) & 1u) && __ldcg(bs + 2 * TH + TW + x - 1) == sa &&
-          __ldcg(bsS + 2 * TH + x - 1) == sb)
-        continue;
-      unite_global(a.tb.nodes, (uint32_t)tile * MS + sa, (uint32_t)tileS * MS + sb, a.tb.err);
-    }
+  const TilePos P = tile_pos<Tl::TW, TH>(a.g, tile);
+  for (int e = threadIdx.x; e < TH + Tl::TW; e += blockDim.x) {
+    uint32_t na, nb;
+    if (border_union<WPR, TH, H>(a, P, tile, e, na, nb)) unite_global(a.tb.nodes, na, nb, a.tb.err);
   }
 }
 
@@ -1017,6 +1037,19 @@ __global__ void phase2_kernel(const SweepArgs a0, const BatchArgs bat) {
 // only its own node, and the parent field it leaves (the root) is an
 // ancestor, so walks of other threads that meet a rewritten node still end
 // at the same root. Phase 3 then reads a slot's decision in one load.
+// Slot node x, whose walk ended at root node `root` with entry v: the root's
+// key and the decision drawn for it (for the Potts model, its new state into
+// nval).
+__device__ __forceinline__ void resolve_write(const SweepArgs& a, uint32_t x, uint32_t root, uint64_t v) {
+  const uint32_t key = (uint32_t)(v >> 32) & 0x7fffffffu;
+  uint32_t f = 0u;
+  if (a.q)
+    a.tb.nval[x] = (uint8_t)potts_new_state(key, a.t, a.ks, a.q);  // §6: the decision is a state
+  else
+    f = decision_bit(key, a.t, a.ks, a.rule);
+  a.tb.nodes[x] = ((uint64_t)(key | (f << 31)) << 32) | root;
+}
+
 template <int WPR, int TH, int H, bool BATCH>
 __device__ __forceinline__ void resolve_body(const SweepArgs& a0, const BatchArgs& bat, int T, int k) {
   constexpr int MS = Tile<WPR, TH, H>::MS;
@@ -1036,13 +1069,7 @@ __device__ __forceinline__ void resolve_body(const SweepArgs& a0, const BatchArg
       cur = (uint32_t)v;
       v = ld_node(a.tb.nodes + cur);
     }
-    const uint32_t key = (uint32_t)(v >> 32) & 0x7fffffffu;
-    uint32_t f = 0u;
-    if (a.q)
-      a.tb.nval[x] = (uint8_t)potts_new_state(key, a.t, a.ks, a.q);  // §6: the decision is a state
-    else
-      f = decision_bit(key, a.t, a.ks, a.rule);
-    a.tb.nodes[x] = ((uint64_t)(key | (f << 31)) << 32) | cur;
+    resolve_write(a, x, cur, v);
   }
 }
 
@@ -1595,7 +1622,9 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
   phase1_body<WPR, TH, H, false, false, true>(S, a, BatchArgs{}, blockIdx.x, 0);
 }
 
-template <int WPR, int TH, int H>
+constexpr int kPottsP3Threads = 256;  // threads per tile of the Potts phase 3
+
+template <int WPR, int TH, int H, int NT>
 struct PottsP3Shared {
   using T = Tile<WPR, TH, H>;
   alignas(16) uint16_t par[TH * T::TW];  // labels from phase 1: par[par[x]] is the tile root of x
@@ -1607,7 +1636,7 @@ struct PottsP3Shared {
   alignas(16) uint32_t bmask[T::RW];     // border roots
   uint32_t pre[T::RW];
   uint32_t wsum[33];
-  long long red[2][T::NT / 32];
+  long long red[2][NT / 32];
 };
 
 // Phase 3 of a q-state Potts sweep for one tile (§6): every cluster takes the
@@ -1616,11 +1645,12 @@ struct PottsP3Shared {
 // E = -(edges joining equal states), M = (sites in state 0) of the new
 // configuration are summed in int64.
 template <int WPR, int TH, int H>
-__global__ void __launch_bounds__(Tile<WPR, TH, H>::NT) potts_phase3_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(kPottsP3Threads) potts_phase3_kernel(const SweepArgs a) {
   using Tl = Tile<WPR, TH, H>;
-  constexpr int TW = Tl::TW, NT = Tl::NT, NB = Tl::NB, MS = Tl::MS, RW = Tl::RW;
+  constexpr int TW = Tl::TW, NT = kPottsP3Threads, NB = Tl::NB, MS = Tl::MS, RW = Tl::RW;
   constexpr int G = TW / 4;  // four-site groups per row
-  __shared__ PottsP3Shared<WPR, TH, H> S;
+  static_assert(RW % NT == 0, "whole rounds of row words");
+  __shared__ PottsP3Shared<WPR, TH, H, NT> S;
   const Geometry& g = a.g;
   const int L = g.L;
   const TilePos P = tile_pos<TW, TH>(g, blockIdx.x);
@@ -1659,22 +1689,41 @@ __global__ void __launch_bounds__(Tile<WPR, TH, H>::NT) potts_phase3_kernel(cons
   }
   __syncthreads();
 
-  // ---- the new state of every tile root (phase 1 marked them)
-  const uint32_t* grb = a.tb.rbits + (size_t)P.tile * RW;
-  for (int rw = tid; rw < RW; rw += NT) {
-    const int y = rw / WPR, w = rw % WPR;
-    if (y >= P.nrows) continue;
-    const uint32_t bm = S.bmask[rw];
-    for (uint32_t m = grb[rw]; m; m &= m - 1) {
-      const int b = __ffs(m) - 1, x = rw * 32 + b;  // tile-local site (row-major, TW = 32 WPR)
-      uint32_t v;
-      if ((bm >> b) & 1u) {
+  // ---- the new state of every tile root (phase 1 marked them): a border
+  // root's from its slot; the inner roots of a warp's row words are listed
+  // (a prefix sum places each lane's roots; the list lives in S.snew, free
+  // until the new states) and drawn 32 at a time, every lane with a root
+  {
+    constexpr int QW = TH * TW / 2 / (NT / 32);  // list entries per warp
+    const uint32_t* grb = a.tb.rbits + (size_t)P.tile * RW;
+    uint16_t* list = reinterpret_cast<uint16_t*>(&S.snew[0][0]) + (tid >> 5) * QW;
+#pragma unroll
+    for (int it = 0; it < RW / NT; ++it) {
+      const int rw = tid + NT * it;  // tile-local sites rw * 32 + b (row-major, TW = 32 WPR)
+      const uint32_t roots = rw / WPR < P.nrows ? grb[rw] : 0u;
+      const uint32_t bm = S.bmask[rw];
+      for (uint32_t m = roots & bm; m; m &= m - 1) {
+        const int x = rw * 32 + __ffs(m) - 1;
         const int sl = slot_of(S.bmask, S.pre, x);
-        v = sl < nsl ? S.slotval[sl] : 0u;
-      } else {
-        v = potts_new_state((uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w + b), a.t, a.ks, a.q);
+        S.val[x] = sl < nsl ? S.slotval[sl] : (uint8_t)0;
       }
-      S.val[x] = (uint8_t)v;
+      const uint32_t inner = roots & ~bm;
+      const int cnt = __popc(inner);
+      const int first = warp_exclusive_sum(cnt, lane);
+      const int total = __shfl_sync(0xffffffffu, first + cnt, 31);
+      for (int r0 = 0; r0 < total; r0 += QW) {  // one round unless most sites are roots
+        int idx = first;
+        for (uint32_t m = inner; m; m &= m - 1, ++idx)
+          if (idx >= r0 && idx < r0 + QW) list[idx - r0] = (uint16_t)(rw * 32 + __ffs(m) - 1);
+        __syncwarp();
+        const int n = min(QW, total - r0);
+        for (int k = lane; k < n; k += 32) {
+          const int x = list[k];
+          const uint32_t key = (uint32_t)(P.y0 + x / TW) * (uint32_t)L + (uint32_t)(P.x0 + x % TW);
+          S.val[x] = (uint8_t)potts_new_state(key, a.t, a.ks, a.q);
+        }
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
@@ -1893,8 +1942,7 @@ cudaError_t launch_potts_phase1(const SweepArgs& a, cudaStream_t st) {
 
 cudaError_t launch_potts_phase3(const SweepArgs& a, cudaStream_t st) {
   constexpr TileShape ts = shape_of(kPottsShape);
-  potts_phase3_kernel<ts.wpr, ts.th, ts.h>
-      <<<a.g.tiles_x * a.g.tiles_y, Tile<ts.wpr, ts.th, ts.h>::NT, 0, st>>>(a);
+  potts_phase3_kernel<ts.wpr, ts.th, ts.h><<<a.g.tiles_x * a.g.tiles_y, kPottsP3Threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,10 +1,10 @@
 """The sweep with phase 3 and the next sweep's phase 1 in one launch.
 
-On tile shapes whose phases 1 and 3 take the same block, a sweep without
-statistics runs phase 3 of sweep t and phase 1 of sweep t + 1 as one launch,
-and a call's last sweep leaves phase 1 of the next sweep done: the next
-sw_sweep call starts at phase 2. These tests split chains into calls of
-every length, put each operation that changes the state or reruns phase 1
+On tile shapes whose phases 1 and 3 take the same block, the sweeps of one
+sw_sweep call without statistics run phase 3 of sweep t and phase 1 of sweep
+t + 1 as one launch; a call's last sweep runs phase 3 alone. These tests
+split chains into calls of every length (one-sweep calls never fuse, longer
+ones do), put the operations that change the state or run phase 1 themselves
 between them (labels, bonds, the equivalence labels, statistics on and off,
 set_state, set_state_async) and check every result against the oracle
 exactly (C8, §2).
@@ -58,7 +58,7 @@ def test_split_calls_with_queries_between(sw, shape, L):
     with make(sw, L, beta, seed, shape) as lat:
         lat.sweep(1)
         assert np.array_equal(lat.spins(), want[1])
-        lat.sweep(2)  # starts from the carried-over phase 1
+        lat.sweep(2)  # one fused launch
         assert np.array_equal(lat.spins(), want[3])
         want_lab, _ = oracle.labels(oracle.bonds(want[3], seed, 3, thr))
         assert np.array_equal(lat.labels(), want_lab)
@@ -86,11 +86,11 @@ def test_split_calls_with_queries_between(sw, shape, L):
 
 @pytest.mark.parametrize("shape", FUSED_SHAPES)
 @pytest.mark.parametrize("asynchronous", [False, True])
-def test_set_state_drops_the_carried_phase1(sw, shape, asynchronous):
+def test_set_state_between_fused_calls(sw, shape, asynchronous):
     L, seed, beta = 257, 77, 0.6
     s = random_spins(L, seed=9, p_minus=0.3)
     with make(sw, L, beta, seed, shape) as lat:
-        lat.sweep(3)  # leaves phase 1 of sweep 3 on the old spins
+        lat.sweep(3)
         if asynchronous:
             lat.set_state_async(s, 40)
         else:
@@ -122,10 +122,9 @@ def test_every_call_length(sw, shape):
         assert np.array_equal(E, want_E) and np.array_equal(M, want_M)
 
 
-def test_trace_growth_keeps_the_carried_row(sw):
-    # the trace holds 1024 sweeps at first: a call that ends at its last row
-    # leaves the next sweep's E/M row zeroed there, and the growth in the next
-    # call must carry it over
+def test_trace_growth_across_fused_calls(sw):
+    # the trace holds 1024 sweeps at first: the next calls grow it while the
+    # fused launches zero each next sweep's E/M row
     L, seed, n1 = 130, 21, 1023
     with make(sw, L, BETA_C, seed, 6) as lat:
         lat.sweep(n1)
