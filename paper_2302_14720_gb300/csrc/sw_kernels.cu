@@ -1252,20 +1252,28 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, int* 
     if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&s_roots_bar)) : "memory");
   }
 
-  // ---- per run: its root's decision; new spins of my strip
+  // ---- per run: its root's decision; new spins of my strip. A row of labels
+  // is 256 bytes, so the rows all start in bank 0, and every row word has a
+  // run start at its column 0: walked in column order, the 32 lanes' first
+  // label loads would meet in two banks. The flip modes walk each word's run
+  // starts cyclically from a lane-dependent column instead (8 strips x 4
+  // words of a warp -> 32 different banks for the first load), record each
+  // run's decision at its start, and spread the decisions over the runs
+  // afterwards with a segmented prefix OR.
+  const int rot = ((k & 7) << 2) | ((w >> 1 & 1) << 1);
   uint32_t snew[H];
 #pragma unroll
   for (int r = 0; r < H; ++r) {
     snew[r] = s[r];
     if (r >= nv || !wmask) continue;
     const int y = y0r + r, base = y * TW + 32 * w;
-    uint32_t R = ~(e_int[r] << 1) & wmask;
-    uint32_t tmask = 0, fprev = 0;
-    while (R) {
-      const int b = __ffs(R) - 1;
-      R &= R - 1;
-      const int rt = par[par[base + b]];  // the run's label, then the label's root
-      if (LABELS) {
+    const uint32_t Rall = ~(e_int[r] << 1) & wmask;  // run starts
+    if (LABELS) {
+      uint32_t R = Rall;
+      while (R) {
+        const int b = __ffs(R) - 1;
+        R &= R - 1;
+        const int rt = par[par[base + b]];  // the run's label, then the label's root
         const int nxt = R ? (__ffs(R) - 1) : nb;
         int key;
         if ((s_bmask[rt >> 5] >> (rt & 31)) & 1u) {
@@ -1276,24 +1284,32 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, int* 
         }
         int32_t* out = a.labels + (size_t)(P.y0 + y) * L + P.x0 + 32 * w;
         for (int x = b; x < nxt; ++x) out[x] = key;
-      } else {
-        const uint32_t f = (s_flip[rt >> 5] >> (rt & 31)) & 1u;
-        tmask |= (f ^ fprev) << b;
-        fprev = f;
+      }
+    } else {
+      uint32_t Rr = __funnelshift_r(Rall, Rall, rot);  // bit i: run start at column (i + rot) mod 32
+      uint32_t D = 0u;                                // decision of each run, at its start
+      while (Rr) {
+        const int b = (__ffs(Rr) - 1 + rot) & 31;
+        Rr &= Rr - 1;
+        const int rt = par[par[base + b]];  // the run's label, then the label's root
+        D |= ((s_flip[rt >> 5] >> (rt & 31)) & 1u) << b;
         if (HIST) {
-          const int nxt = R ? (__ffs(R) - 1) : nb;
-          atomicAdd(&s_size[rt], nxt - b);
+          const uint32_t above = Rall & ~((2u << b) - 1u);  // run starts after b (b = 31: none)
+          atomicAdd(&s_size[rt], (above ? __ffs(above) - 1 : nb) - b);
         }
       }
-    }
-    if (!LABELS) {
-      // prefix xor turns "decision changes at this run start" into per-site flips
-      tmask ^= tmask << 1;
-      tmask ^= tmask << 2;
-      tmask ^= tmask << 4;
-      tmask ^= tmask << 8;
-      tmask ^= tmask << 16;
-      snew[r] = (a.rule ? 0u : s[r]) ^ (tmask & wmask);
+      // segmented prefix OR: a site takes the decision of its run's start
+      uint32_t G = ~Rall;  // sites that continue the run of the site before them
+      D |= (D << 1) & G;
+      G &= G << 1;
+      D |= (D << 2) & G;
+      G &= G << 2;
+      D |= (D << 4) & G;
+      G &= G << 4;
+      D |= (D << 8) & G;
+      G &= G << 8;
+      D |= (D << 16) & G;
+      snew[r] = (a.rule ? 0u : s[r]) ^ (D & wmask);
       store_spin_bits(a.spins_out + (size_t)(P.y0 + y) * L + P.x0 + 32 * w, snew[r], nb, g.aligned16);
     }
   }
