@@ -1104,7 +1104,7 @@ struct P3Shared {
 // Returns false when the labels' bulk copy did not land (the CTA's shared
 // memory may still be written by it: the caller must not reuse it).
 template <int WPR, int TH, int H, int MODE, bool BATCH>
-__device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, int* s_size, const SweepArgs& a0,
+__device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, uint32_t* s_size, const SweepArgs& a0,
                                             const BatchArgs& bat, int T, int ksweep) {
   using Tl = Tile<WPR, TH, H>;
   constexpr int TW = Tl::TW, NT = Tl::NT, NB = Tl::NB, MS = Tl::MS, BBW = Tl::BBW, RW = Tl::RW;
@@ -1151,10 +1151,10 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, int* 
     s[r] = tb[rw];
     e_int[r] = tb[RW + rw] & ~lbit;
     s_bmask[rw] = gbm[rw];
-    if (HIST) {
-      int4* z = reinterpret_cast<int4*>(s_size + base);
+    if (HIST) {  // the 32 sizes of this row word: 16 words of two 16-bit counters
+      int4* z = reinterpret_cast<int4*>(s_size + base / 2);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) z[q] = make_int4(0, 0, 0, 0);
+      for (int q = 0; q < 4; ++q) z[q] = make_int4(0, 0, 0, 0);
     }
   }
   if (HIST)
@@ -1261,6 +1261,11 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, int* 
   // run's decision at its start, and spread the decisions over the runs
   // afterwards with a segmented prefix OR.
   const int rot = ((k & 7) << 2) | ((w >> 1 & 1) << 1);
+  // HIST: a lane adds up the lengths of consecutive runs of one root and
+  // sends the sum when the root changes (a tile's runs mostly belong to few
+  // clusters near order, which made per-run shared atomics serialise)
+  int acc_rt = -1;
+  uint32_t acc_len = 0u;
   uint32_t snew[H];
 #pragma unroll
   for (int r = 0; r < H; ++r) {
@@ -1295,7 +1300,14 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, int* 
         D |= ((s_flip[rt >> 5] >> (rt & 31)) & 1u) << b;
         if (HIST) {
           const uint32_t above = Rall & ~((2u << b) - 1u);  // run starts after b (b = 31: none)
-          atomicAdd(&s_size[rt], (above ? __ffs(above) - 1 : nb) - b);
+          const uint32_t len = (uint32_t)((above ? __ffs(above) - 1 : nb) - b);
+          if (rt == acc_rt) {
+            acc_len += len;
+          } else {
+            if (acc_rt >= 0) atomicAdd(&s_size[acc_rt >> 1], acc_len << ((acc_rt & 1) << 4));
+            acc_rt = rt;
+            acc_len = len;
+          }
         }
       }
       // segmented prefix OR: a site takes the decision of its run's start
@@ -1314,6 +1326,12 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, int* 
     }
   }
   if (LABELS) return true;
+  if (HIST) {  // the lanes' last sums: one atomic per root and warp
+    __syncwarp();
+    const uint32_t peers = __match_any_sync(0xffffffffu, acc_rt);
+    const uint32_t sum = __reduce_add_sync(peers, acc_len);
+    if (acc_rt >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_size[acc_rt >> 1], sum << ((acc_rt & 1) << 4));
+  }
 #pragma unroll
   for (int r = 0; r < H; ++r) s_snew[y0r + r][w] = snew[r];
 
@@ -1381,29 +1399,50 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, int* 
   }
 
   if (HIST) {
-    // sizes are complete after this barrier: bin inner clusters here, send
-    // border pieces to their global root
+    // sizes are complete after this barrier: bin the inner clusters (the
+    // tile roots phase 1 marked, less the border roots), send border pieces
+    // to their global root. Counts, sums of squares (at most 8192^2 a tile)
+    // and bins 0-7 (8-bit fields: at most 64 roots a thread) add up in
+    // registers and once per warp into the shared histogram.
     __syncthreads();
+    const uint32_t* grb = a.tb.rbits + (size_t)P.tile * RW;
+    uint32_t cnt = 0u, sq = 0u, bins03 = 0u, bins47 = 0u;
 #pragma unroll
     for (int r = 0; r < H; ++r) {
-      if (r >= nv) break;
+      if (r >= nv || !wmask) continue;
       const int base = (y0r + r) * TW + 32 * w, rw = (y0r + r) * WPR + w;
-      uint32_t R = ~(e_int[r] << 1) & wmask;
-      while (R) {
-        const int b = __ffs(R) - 1;
-        R &= R - 1;
-        const int l = base + b;
-        if (par[l] != l) continue;
-        const uint32_t sz = (uint32_t)s_size[l];
-        if ((s_bmask[rw] >> b) & 1u) {
+      const uint32_t bm = s_bmask[rw];
+      for (uint32_t m = grb[rw]; m; m &= m - 1) {
+        const int b = __ffs(m) - 1, l = base + b;
+        const uint32_t sz = (s_size[l >> 1] >> ((l & 1) << 4)) & 0xffffu;
+        if ((bm >> b) & 1u) {
           const int sl = slot_of(s_bmask, s_pre, l);
           if (sl < nsl) atomicAdd(&a.csize[s_slotroot[sl]], sz);
         } else {
-          atomicAdd(&s_hist[0], 1ull);
-          atomicAdd(&s_hist[1], (unsigned long long)sz * sz);
-          atomicAdd(&s_hist[2 + log2_floor(sz)], 1ull);
+          const int bin = log2_floor(sz);
+          cnt += 1u;
+          sq += sz * sz;
+          if (bin < 4) bins03 += 1u << (8 * bin);
+          else if (bin < 8) bins47 += 1u << (8 * (bin - 4));
+          else atomicAdd(&s_hist[2 + bin], 1ull);
         }
       }
+    }
+    __syncwarp();
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    sq = __reduce_add_sync(0xffffffffu, sq);
+    uint32_t bsum[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      bsum[q] = __reduce_add_sync(0xffffffffu, (bins03 >> (8 * q)) & 0xffu);
+      bsum[4 + q] = __reduce_add_sync(0xffffffffu, (bins47 >> (8 * q)) & 0xffu);
+    }
+    if (lane == 0) {
+      if (cnt) atomicAdd(&s_hist[0], (unsigned long long)cnt);
+      if (sq) atomicAdd(&s_hist[1], (unsigned long long)sq);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (bsum[q]) atomicAdd(&s_hist[2 + q], (unsigned long long)bsum[q]);
     }
   }
   __syncthreads();
@@ -1430,7 +1469,7 @@ template <int WPR, int TH, int H, int MODE, bool BATCH>
 __global__ void __launch_bounds__(WPR * (TH / H), strip_min_blocks<WPR * (TH / H), H>())
     phase3_kernel(const SweepArgs a0, const BatchArgs bat) {
   __shared__ P3Shared<WPR, TH, H, MODE> S;
-  extern __shared__ __align__(16) int s_size[];  // HIST: [TH * TW]
+  extern __shared__ __align__(16) uint32_t s_size[];  // HIST: [TH * TW / 2], two 16-bit sizes a word
   phase3_body<WPR, TH, H, MODE, BATCH>(S, s_size, a0, bat, blockIdx.x, 0);
 }
 
@@ -1868,7 +1907,7 @@ cudaError_t launch_all(int which, const SweepArgs& a, int mode, uint8_t* out, cu
       if (mode == 0) {
         phase3_kernel<WPR, TH, H, 0, false><<<ntiles, T::NT, 0, st>>>(a, BatchArgs{});
       } else if (mode == 1) {
-        const size_t dyn = (size_t)TH * T::TW * sizeof(int);
+        const size_t dyn = (size_t)TH * T::TW * sizeof(uint16_t);
         static bool attr_done = false;
         if (!attr_done) {
           cudaError_t e = cudaFuncSetAttribute(phase3_kernel<WPR, TH, H, 1, false>,
