@@ -59,9 +59,11 @@ RW = (TW // 32) * TH  # 32-site row-words per tile
 # the stored layout (bit masks, 16-bit tile roots, border tables); slot nodes
 # (8 bytes per border component) are data dependent and not counted.
 PHASE_BYTES_PER_TILE = {
-    # spins + halo in; spin/east/south masks, 16-bit tile roots, border-root
-    # and root masks, border slots, tile bits, slot count out
-    0: (TW * TH + TH + TW) + (3 * RW * 4 + 2 * TW * TH + 2 * 4 * RW + 2 * NB + 4 * BBW + 4),
+    # spins + halo and the bond draws (two 32-bit masks per row word, drawn
+    # during the previous sweep's merge) in; spin/east/south masks, 16-bit
+    # tile roots, border-root and root masks, border slots, tile bits, slot
+    # count out
+    0: (TW * TH + TH + TW + 8 * RW) + (3 * RW * 4 + 2 * TW * TH + 2 * 4 * RW + 2 * NB + 4 * BBW + 4),
     # spin/east masks, roots, border-root and root masks, slot count, tile
     # bits, neighbours' halo slots in; spins out
     2: (2 * RW * 4 + 2 * TW * TH + 2 * 4 * RW + 4 + 4 * BBW + 2 * (TH + TW)) + TW * TH,
@@ -71,7 +73,8 @@ PHASE_BYTES_PER_TILE = {
 # border slot its node (read in the union walks, rewritten by the resolve
 # pass); the slot count is data dependent, so the model counts every border
 # site as a slot (an upper bound of the algorithmic bytes).
-PHASE_BYTES_PER_TILE[1] = 4 * BBW + 2 * (NB + TH + TW) + 4 + 3 * 8 * NB
+# The next sweep's bond draws go out as well.
+PHASE_BYTES_PER_TILE[1] = 4 * BBW + 2 * (NB + TH + TW) + 4 + 3 * 8 * NB + 8 * RW
 # Phase 3 of a sweep with phase 1 of the next in one launch: both kernels'
 # bytes, less the spins and halo that phase 1 then takes from shared memory.
 PHASE_BYTES_PER_TILE[4] = PHASE_BYTES_PER_TILE[0] + PHASE_BYTES_PER_TILE[2] - (TW * TH + TH + TW)
@@ -79,11 +82,12 @@ PHASE_NAMES = {0: "phase1_bonds_tile_ccl", 1: "phase2_merge_resolve", 2: "phase3
                4: "phase3_with_next_phase1"}
 SWEEP_MODEL_BYTES_PER_SITE = 10  # read spins, write+read int32 labels, write spins
 # q-state Potts sweep (§6) on the same tiles: phase 1 and phase 2 + resolve
-# as for Ising (the state bytes take the place of the spins); phase 3 reads
+# as for Ising (the state bytes take the place of the spins; phase 1 draws
+# its own bonds); phase 3 reads
 # the 16-bit tile roots, border-root and root masks, slot count, the tile's
 # slot states and the halo's slots and slot states, and writes the states.
 MS = 2 * (TW + TH)
-POTTS_BYTES_PER_TILE = (PHASE_BYTES_PER_TILE[0] + PHASE_BYTES_PER_TILE[1]
+POTTS_BYTES_PER_TILE = (PHASE_BYTES_PER_TILE[0] - 8 * RW + PHASE_BYTES_PER_TILE[1] - 8 * RW
                         + 2 * TW * TH + 2 * 4 * RW + 4 + MS + 3 * (TH + TW) + TW * TH)
 
 
@@ -434,6 +438,8 @@ def run_ours(args):
     stream2 = torch.cuda.Stream()
     lat2 = sw.Lattice(L, BETA, seed + 1000, sw.SW_INIT_HOT, stream=stream2.cuda_stream)
     pair = [lat, lat2]
+    # Each lattice's steps take consecutive counters (a chain whose state
+    # goes through host memory between sweeps).
     e2e_steps = max(4, min(args.steps, 20))
     t = lat.t
     for k in range(2):  # warm-up of both lattices (allocates their staging buffers)
@@ -444,12 +450,12 @@ def run_ours(args):
     t0 = time.perf_counter()
     pending = None
     for k in range(e2e_steps):
-        h = pair[k % 2]
-        sw.sw_set_state_async(h.h, host_np, t + k)     # H2D: the step's input state (checked on the GPU)
+        h, tk = pair[k % 2], t + 1 + k // 2
+        sw.sw_set_state_async(h.h, host_np, tk)        # H2D: the step's input state (checked on the GPU)
         h.sweep(1)
         if pending is not None:
             pending[0].observables(pending[1], 1)      # D2H: the previous step's E and M
-        pending = (h, t + k)
+        pending = (h, tk)
     pending[0].observables(pending[1], 1)
     e2e_total = time.perf_counter() - t0
     e2e_value = world * N_SITES * e2e_steps / max_over_ranks(e2e_total, world)
@@ -564,6 +570,17 @@ def measure_other_configs(sw, torch, stream, flush):
             tot += timed_sweeps(torch, stream, lambda: lat.sweep(1), 1)
         lat.observables(3, 10)
     out["L8192_beta0.50"] = {"su_s": N_SITES * 10 / (tot / 1e3), "ms_per_sweep": tot / 10, "sweeps": 10}
+    # The headline lattice as a chain: 200 consecutive sweeps in one
+    # sw_sweep call (phase 3 and the next sweep's phase 1 in one launch, the
+    # merge phases drawing the next sweep's bonds); a sweep moves ~0.5 GB,
+    # well above L2, so no flush is needed between sweeps.
+    with sw.Lattice(L, BETA, SEED, stream=stream.cuda_stream) as lat:
+        lat.sweep(20)
+        n = 200
+        ms = timed_sweeps(torch, stream, lambda: lat.sweep(n), n)
+        lat.observables(20, n)
+    out["L8192_betac_chain"] = {"su_s": N_SITES * n / (ms / 1e3), "ms_per_sweep": ms / n, "sweeps": n,
+                                "how": "one sw_sweep(200) call, CUDA events around it"}
     # the paper's label-equivalence labelling (§2.3) against the tile
     # union-find, both from the same state (each includes drawing the bonds)
     out["labels_union_find_vs_equivalence"] = {}

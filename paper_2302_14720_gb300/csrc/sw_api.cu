@@ -111,6 +111,12 @@ struct sw_lattice {
   int32_t* nslots2 = nullptr;
   uint64_t* nodes2 = nullptr;
   bool fuse = false;       // the tile shape has the phase31 launch
+  // The bond draws of sweep draws_t (C5 depends on the seed, the counter and
+  // the site, not on the spins): the merge phases of a sweep leave those of
+  // the next sweep here when the two run in one call with the fused launch;
+  // any later phase 1 of counter draws_t may read them too; -1: none held.
+  uint2* draws = nullptr;
+  int64_t draws_t = -1;
   int8_t* spins = nullptr;
   uint32_t* csize = nullptr;
   int64_t* em = nullptr;    // [cap][2]
@@ -137,7 +143,7 @@ namespace {
 
 void free_all(sw_lattice* h) {
   void* ptrs[] = {h->spins, h->tb.tbits, h->tb.roots, h->tb.bmask, h->tb.rbits, h->tb.nodes, h->tb.bslot, h->tb.bbits, h->tb.nslots, h->tb.err,
-                  h->bslot2, h->nslots2, h->nodes2,
+                  h->bslot2, h->nslots2, h->nodes2, h->draws,
                   h->csize, h->em, h->hist, h->label_buf, h->bond_buf, h->ref_buf, h->le_flag, h->staging,
                   h->check_flag};
   for (void* p : ptrs)
@@ -206,6 +212,7 @@ sw::SweepArgs args_of(const sw_lattice* h, int64_t t = -1) {
   }
   a.spins_in = h->spins;
   a.spins_out = h->spins;
+  if (h->draws && h->draws_t == t) a.draws_in = h->draws;
   return a;
 }
 
@@ -332,6 +339,7 @@ int sw_create(int32_t L, double beta, uint64_t seed, int32_t init, void* stream,
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.nslots, ntiles * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->tb.err, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->csize, ntiles * ts.max_slots() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->draws, ntiles * ts.row_words() * sizeof(uint2));
   h->fuse = sw::batch_fused_supported(h->shape);
   if (e == cudaSuccess && h->fuse) e = cudaMalloc(&h->nodes2, ntiles * ts.max_slots() * sizeof(uint64_t));
   if (e == cudaSuccess && h->fuse) e = cudaMalloc(&h->bslot2, ntiles * ts.boundary_sites() * sizeof(uint16_t));
@@ -401,9 +409,16 @@ int sw_sweep(sw_lattice* h, int32_t n) {
     if (!carried)
       SW_CUDA(timed_phase(h, 0, [&] { return sw::launch_phase1(h->shape, a, h->stream); }), "phase 1 launch");
     carried = false;
+    // Before the fused launch, the merge phases also draw the next sweep's
+    // bonds, which the launch's phase 1 part then reads (phase 1 alone is
+    // faster drawing them itself: measured at L = 8192).
+    const bool fuse_next = fused && k + 1 < n;
+    if (fuse_next) a.draws_out = h->draws;
     SW_CUDA(timed_phase(h, 1, [&] { return sw::launch_phase2(h->shape, a, h->stream); }), "phase 2 launch");
+    if (fuse_next) h->draws_t = h->t + 1;
+    a.draws_out = nullptr;
     if (!h->hist_on) a.hist = nullptr;
-    if (fused && k + 1 < n) {
+    if (fuse_next) {
       sw::SweepArgs a1 = args_of(h, h->t + 1);
       a1.em = h->em + 2 * (row + 1);  // zeroed by the next sweep's phase 1
       a1.hist = nullptr;

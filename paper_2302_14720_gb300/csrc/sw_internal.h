@@ -86,6 +86,11 @@ struct SweepArgs {
   int64_t* hist;       // flip mode: SW_HIST_WORDS accumulators or nullptr
   uint32_t* csize;     // flip mode with hist: per-node cluster size accumulators [nodes]
   int32_t* labels;     // labels mode: int32 [L][L] output
+  // The C5 draws of a sweep depend on the seed, the counter and the site,
+  // not on the spins, so they can be taken ahead of time: per row word of a
+  // tile ([ntiles][row_words]) the mask of east and of south words below thr.
+  const uint2* draws_in;  // phase 1: the draws of sweep t, or nullptr (phase 1 draws them)
+  uint2* draws_out;       // phase 2 + resolve: where to leave the draws of sweep t + 1, or nullptr
 };
 
 inline int ntiles_of(const Geometry& g) { return g.tiles_x * g.tiles_y; }

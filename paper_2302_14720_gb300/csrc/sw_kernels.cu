@@ -510,6 +510,55 @@ __device__ __forceinline__ bool cta_args(const SweepArgs& a0, const BatchArgs& b
 
 // ================================================================ phase 1
 
+// The bond draws (C5) of the row word of sites i0 .. i0 + nb - 1 in sweep t:
+// bit b of .x (.y) is set iff the east (south) word of site i0 + b is below
+// thr. Site i takes words x0 (east) and x1 (south) of block (i >> 1, t, 0, 0)
+// when i is even, x2 and x3 when it is odd.
+__device__ __forceinline__ uint2 bond_draws(uint32_t i0, int nb, int L, uint32_t t, uint32_t thr,
+                                            const KeySchedule& ks) {
+  uint32_t rE = 0u, rS = 0u;
+  if ((L & 1) == 0) {
+    // even L: sites i0+b, i0+b+1 (b even) share Philox block (i0+b)/2
+    if (nb == 32) {
+      // a whole word: each comparison is the carry of one subtraction, added
+      // into the mask as its new lowest bit (a set carry: q >= thr, no bond),
+      // so site 0 ends at bit 31; one bit reversal and a complement at the
+      // end. Fewer integer-pipe operations than a compare and a select each.
+#pragma unroll 4
+      for (int b = 0; b < 32; b += 2) {
+        const uint4 q = philox4x32_10(make_uint4((i0 + b) >> 1, t, 0u, 0u), ks);
+        asm("{\n\t.reg .u32 d;\n\t"
+            "sub.cc.u32 d, %2, %6;\n\taddc.u32 %0, %0, %0;\n\t"
+            "sub.cc.u32 d, %4, %6;\n\taddc.u32 %0, %0, %0;\n\t"
+            "sub.cc.u32 d, %3, %6;\n\taddc.u32 %1, %1, %1;\n\t"
+            "sub.cc.u32 d, %5, %6;\n\taddc.u32 %1, %1, %1;\n\t}"
+            : "+r"(rE), "+r"(rS)
+            : "r"(q.x), "r"(q.y), "r"(q.z), "r"(q.w), "r"(thr));
+      }
+      rE = __brev(~rE);
+      rS = __brev(~rS);
+    } else {
+#pragma unroll 4
+      for (int b = 0; b < 32; b += 2) {
+        if (b < nb) {
+          const uint4 q = philox4x32_10(make_uint4((i0 + b) >> 1, t, 0u, 0u), ks);
+          rE |= ((uint32_t)(q.x < thr) << b) | ((uint32_t)(q.z < thr) << (b + 1));
+          rS |= ((uint32_t)(q.y < thr) << b) | ((uint32_t)(q.w < thr) << (b + 1));
+        }
+      }
+    }
+  } else {
+    for (int b = 0; b < nb; ++b) {
+      const uint32_t i = i0 + b;
+      const uint4 q = philox4x32_10(make_uint4(i >> 1, t, 0u, 0u), ks);
+      const uint32_t we = (i & 1u) ? q.z : q.x, ws = (i & 1u) ? q.w : q.y;
+      rE |= (uint32_t)(we < thr) << b;
+      rS |= (uint32_t)(ws < thr) << b;
+    }
+  }
+  return make_uint2(rE, rS);
+}
+
 // Phase 1 runs one warp per 32-column band and asks for 1280 resident
 // threads an SM (at most 51 registers a thread; ten CTAs of 128 threads also
 // fit their shared memory).
@@ -671,35 +720,15 @@ __device__ __forceinline__ void phase1_body(P1Shared<WPR, TH, H>& S, const Sweep
     }
     uint32_t rE = 0, rS = 0;
     if (vmask) {
-      const uint32_t i0 = (uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w);
-      if ((L & 1) == 0) {
-        // even L: sites i0+b, i0+b+1 (b even) share Philox block (i0+b)/2
-        if (nb == 32) {
-          // a whole word: the pair bits shift in from the top, 2 per block
-#pragma unroll 4
-          for (int b = 0; b < 32; b += 2) {
-            const uint4 q = philox4x32_10(make_uint4((i0 + b) >> 1, a.t, 0u, 0u), a.ks);
-            rE = (rE >> 2) | ((uint32_t)(q.x < a.thr) << 30) | ((uint32_t)(q.z < a.thr) << 31);
-            rS = (rS >> 2) | ((uint32_t)(q.y < a.thr) << 30) | ((uint32_t)(q.w < a.thr) << 31);
-          }
-        } else {
-#pragma unroll 4
-          for (int b = 0; b < 32; b += 2) {
-            if (b < nb) {
-              const uint4 q = philox4x32_10(make_uint4((i0 + b) >> 1, a.t, 0u, 0u), a.ks);
-              rE |= ((uint32_t)(q.x < a.thr) << b) | ((uint32_t)(q.z < a.thr) << (b + 1));
-              rS |= ((uint32_t)(q.y < a.thr) << b) | ((uint32_t)(q.w < a.thr) << (b + 1));
-            }
-          }
-        }
+      if (a.draws_in) {
+        const uint2 d = __ldcs(a.draws_in + (size_t)P.tile * RW + rw);
+        rE = d.x;
+        rS = d.y;
       } else {
-        for (int b = 0; b < nb; ++b) {
-          const uint32_t i = i0 + b;
-          const uint4 q = philox4x32_10(make_uint4(i >> 1, a.t, 0u, 0u), a.ks);
-          const uint32_t we = (i & 1u) ? q.z : q.x, ws = (i & 1u) ? q.w : q.y;
-          rE |= (uint32_t)(we < a.thr) << b;
-          rS |= (uint32_t)(ws < a.thr) << b;
-        }
+        const uint2 d = bond_draws((uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w), nb, L, a.t,
+                                   a.thr, a.ks);
+        rE = d.x;
+        rS = d.y;
       }
     }
     const uint32_t e = eqE & rE, d = eqS & rS;
@@ -1021,8 +1050,45 @@ __device__ __forceinline__ void phase2_body(const SweepArgs& a0, const BatchArgs
   }
 }
 
+// ------------------------------------------------ bond draws of the next sweep
+//
+// The bond draws of sweep t + 1 (C5) depend on the seed, the counter and the
+// site, not on the spins, so they are taken during the cross-tile merge of
+// sweep t: the merge's walks are chains of dependent L2 loads that leave the
+// SMs' integer multiply pipes idle, and the Philox rounds are bound by
+// those. kDrawWarps extra warps of every phase 2 and resolve CTA draw a share
+// of their tile's row words (the first draw_split in phase 2, the rest in
+// resolve) into a.draws_out; phase 1 of sweep t + 1 reads them.
+constexpr int kDrawWarps = 2;
+template <int RW>
+constexpr int draw_split() {
+  return RW - RW / 4;
+}
+
+template <int WPR, int TH, int H>
+__device__ __forceinline__ void draw_next_bonds(const SweepArgs& a, int tile, int d, int rw0, int rw1) {
+  using Tl = Tile<WPR, TH, H>;
+  constexpr int RW = Tl::RW;
+  const TilePos P = tile_pos<Tl::TW, TH>(a.g, tile);
+  const int L = a.g.L;
+  for (int rw = rw0 + d; rw < rw1; rw += 32 * kDrawWarps) {
+    const int y = rw / WPR, w = rw % WPR;
+    const int nb = max(0, min(32, P.ncols - 32 * w));
+    if (y < P.nrows && nb > 0)
+      __stcs(a.draws_out + (size_t)tile * RW + rw,
+             bond_draws((uint32_t)(P.y0 + y) * (uint32_t)L + (uint32_t)(P.x0 + 32 * w), nb, L, a.t + 1u, a.thr, a.ks));
+  }
+}
+
+// With a.draws_out the block has kDrawWarps more warps than edges (TH + TW
+// threads); they draw the first draw_split row words of the tile.
 template <int WPR, int TH, int H, bool BATCH>
 __global__ void phase2_kernel(const SweepArgs a0, const BatchArgs bat) {
+  using Tl = Tile<WPR, TH, H>;
+  if (!BATCH && a0.draws_out && threadIdx.x >= TH + Tl::TW) {
+    draw_next_bonds<WPR, TH, H>(a0, blockIdx.x, threadIdx.x - (TH + Tl::TW), 0, draw_split<Tl::RW>());
+    return;
+  }
   phase2_body<WPR, TH, H, BATCH>(a0, bat, blockIdx.x, 0);
 }
 
@@ -1050,14 +1116,15 @@ __device__ __forceinline__ void resolve_write(const SweepArgs& a, uint32_t x, ui
   a.tb.nodes[x] = ((uint64_t)(key | (f << 31)) << 32) | root;
 }
 
+// nthr: the threads that walk slots (the first nthr of the block).
 template <int WPR, int TH, int H, bool BATCH>
-__device__ __forceinline__ void resolve_body(const SweepArgs& a0, const BatchArgs& bat, int T, int k) {
+__device__ __forceinline__ void resolve_body(const SweepArgs& a0, const BatchArgs& bat, int T, int k, int nthr) {
   constexpr int MS = Tile<WPR, TH, H>::MS;
   SweepArgs a;
   int tile;
   if (!cta_args<BATCH>(a0, bat, T, k, a, tile)) return;
   const int nsl = min(a.tb.nslots[tile], MS);
-  for (int j = threadIdx.x; j < nsl; j += blockDim.x) {
+  for (int j = threadIdx.x; j < nsl; j += nthr) {
     const uint32_t x = (uint32_t)tile * MS + j;
     uint32_t cur = x;
     uint64_t v = ld_node(a.tb.nodes + cur);
@@ -1073,9 +1140,18 @@ __device__ __forceinline__ void resolve_body(const SweepArgs& a0, const BatchArg
   }
 }
 
+// Slot walks by the first kResolveThreads threads; with a.draws_out,
+// kDrawWarps more warps draw the tile's row words from draw_split on.
+constexpr int kResolveThreads = 128;
 template <int WPR, int TH, int H, bool BATCH>
 __global__ void resolve_kernel(const SweepArgs a0, const BatchArgs bat) {
-  resolve_body<WPR, TH, H, BATCH>(a0, bat, blockIdx.x, 0);
+  using Tl = Tile<WPR, TH, H>;
+  if (threadIdx.x >= kResolveThreads) {
+    if (!BATCH && a0.draws_out)
+      draw_next_bonds<WPR, TH, H>(a0, blockIdx.x, threadIdx.x - kResolveThreads, draw_split<Tl::RW>(), Tl::RW);
+    return;
+  }
+  resolve_body<WPR, TH, H, BATCH>(a0, bat, blockIdx.x, 0, kResolveThreads);
 }
 
 // ================================================================ phase 3
@@ -1170,6 +1246,45 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, uint3
     if (LABELS) s_slotkey[j] = (int)((uint32_t)(v >> 32) & 0x7fffffffu);
     else if (v >> 63) atomicOr(&s_slotdec[j >> 5], 1u << (j & 31));
     if (HIST) s_slotroot[j] = (uint32_t)v;
+  }
+  if (!LABELS) {
+    // ---- new spins of the halo sites: old spin (phase 1) xor their cluster's
+    // flip; the two dependent loads (slot, then node) overlap the labels copy
+    const uint32_t* bbits = a.tb.bbits + (size_t)P.tile * BBW;
+    for (int b0 = warp0; b0 < TH; b0 += NT) {
+      const int y = b0 + lane;
+      bool bit = false;
+      if (y < P.nrows) {
+        const int tileE = P.ty * g.tiles_x + (P.tx + 1) % g.tiles_x;
+        uint16_t slot = __ldcg(a.tb.bslot + (size_t)tileE * NB + y);
+        if (slot >= MS) {
+          atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+          slot = 0;
+        }
+        const uint64_t v = ld_node(a.tb.nodes + (uint32_t)tileE * MS + slot);
+        const uint32_t old = (bbits[Tl::OFF_HE + (y >> 5)] >> (y & 31)) & 1u;
+        bit = ((a.rule ? 0u : old) ^ (uint32_t)(v >> 63)) != 0u;
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, bit);
+      if (lane == 0) s_hEnew[b0 >> 5] = m;
+    }
+    for (int b0 = warp0; b0 < TW; b0 += NT) {
+      const int x = b0 + lane;
+      bool bit = false;
+      if (x < P.ncols) {
+        const int tileS = ((P.ty + 1) % g.tiles_y) * g.tiles_x + P.tx;
+        uint16_t slot = __ldcg(a.tb.bslot + (size_t)tileS * NB + 2 * TH + x);
+        if (slot >= MS) {
+          atomicCAS(a.tb.err, 0, kErrSlotOverflow);
+          slot = 0;
+        }
+        const uint64_t v = ld_node(a.tb.nodes + (uint32_t)tileS * MS + slot);
+        const uint32_t old = (bbits[Tl::OFF_HS + (x >> 5)] >> (x & 31)) & 1u;
+        bit = ((a.rule ? 0u : old) ^ (uint32_t)(v >> 63)) != 0u;
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, bit);
+      if (lane == 0) s_hSnew[b0 >> 5] = m;
+    }
   }
   __syncthreads();
 
@@ -1335,42 +1450,6 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, uint3
 #pragma unroll
   for (int r = 0; r < H; ++r) s_snew[y0r + r][w] = snew[r];
 
-  // ---- new spins of the halo sites: old spin (phase 1) xor their cluster's flip
-  const uint32_t* bbits = a.tb.bbits + (size_t)P.tile * BBW;
-  for (int b0 = warp0; b0 < TH; b0 += NT) {
-    const int y = b0 + lane;
-    bool bit = false;
-    if (y < P.nrows) {
-      const int tileE = P.ty * g.tiles_x + (P.tx + 1) % g.tiles_x;
-      uint16_t slot = __ldcg(a.tb.bslot + (size_t)tileE * NB + y);
-      if (slot >= MS) {
-        atomicCAS(a.tb.err, 0, kErrSlotOverflow);
-        slot = 0;
-      }
-      const uint64_t v = ld_node(a.tb.nodes + (uint32_t)tileE * MS + slot);
-      const uint32_t old = (bbits[Tl::OFF_HE + (y >> 5)] >> (y & 31)) & 1u;
-      bit = ((a.rule ? 0u : old) ^ (uint32_t)(v >> 63)) != 0u;
-    }
-    const uint32_t m = __ballot_sync(0xffffffffu, bit);
-    if (lane == 0) s_hEnew[b0 >> 5] = m;
-  }
-  for (int b0 = warp0; b0 < TW; b0 += NT) {
-    const int x = b0 + lane;
-    bool bit = false;
-    if (x < P.ncols) {
-      const int tileS = ((P.ty + 1) % g.tiles_y) * g.tiles_x + P.tx;
-      uint16_t slot = __ldcg(a.tb.bslot + (size_t)tileS * NB + 2 * TH + x);
-      if (slot >= MS) {
-        atomicCAS(a.tb.err, 0, kErrSlotOverflow);
-        slot = 0;
-      }
-      const uint64_t v = ld_node(a.tb.nodes + (uint32_t)tileS * MS + slot);
-      const uint32_t old = (bbits[Tl::OFF_HS + (x >> 5)] >> (x & 31)) & 1u;
-      bit = ((a.rule ? 0u : old) ^ (uint32_t)(v >> 63)) != 0u;
-    }
-    const uint32_t m = __ballot_sync(0xffffffffu, bit);
-    if (lane == 0) s_hSnew[b0 >> 5] = m;
-  }
   __syncthreads();
 
   // ---- E and M of the new state (C10)
@@ -1582,7 +1661,7 @@ __global__ void __launch_bounds__(32 * WPR, band_min_blocks<32 * WPR>())
     if (!grid_sync(b.gbar, b.err)) return;
     for (int T = blockIdx.x; T < ntiles; T += gridDim.x) phase2_body<WPR, TH, H, true>(none, b, T, k);
     if (!grid_sync(b.gbar, b.err)) return;
-    for (int T = blockIdx.x; T < ntiles; T += gridDim.x) resolve_body<WPR, TH, H, true>(none, b, T, k);
+    for (int T = blockIdx.x; T < ntiles; T += gridDim.x) resolve_body<WPR, TH, H, true>(none, b, T, k, blockDim.x);
     if (!grid_sync(b.gbar, b.err)) return;
     for (int T = blockIdx.x; T < ntiles; T += gridDim.x) {
       const bool ok = phase3_body<WPR, TH, H, 0, true>(U.p3, nullptr, none, b, T, k);
@@ -1900,8 +1979,11 @@ cudaError_t launch_all(int which, const SweepArgs& a, int mode, uint8_t* out, cu
       phase1_kernel<WPR, TH, H, false><<<ntiles, 32 * WPR, 0, st>>>(a, BatchArgs{});
       break;
     case 2:
-      phase2_kernel<WPR, TH, H, false><<<ntiles, TH + T::TW, 0, st>>>(a, BatchArgs{});
-      resolve_kernel<WPR, TH, H, false><<<ntiles, 128, 0, st>>>(a, BatchArgs{});
+      {
+        const int xd = a.draws_out ? 32 * kDrawWarps : 0;  // the warps that draw the next sweep's bonds
+        phase2_kernel<WPR, TH, H, false><<<ntiles, TH + T::TW + xd, 0, st>>>(a, BatchArgs{});
+        resolve_kernel<WPR, TH, H, false><<<ntiles, kResolveThreads + xd, 0, st>>>(a, BatchArgs{});
+      }
       break;
     case 3:
       if (mode == 0) {
@@ -1925,7 +2007,7 @@ cudaError_t launch_all(int which, const SweepArgs& a, int mode, uint8_t* out, cu
       break;
     case 12:
       phase2_kernel<WPR, TH, H, true><<<ntiles, TH + T::TW, 0, st>>>(a, *batch);
-      resolve_kernel<WPR, TH, H, true><<<ntiles, 128, 0, st>>>(a, *batch);
+      resolve_kernel<WPR, TH, H, true><<<ntiles, kResolveThreads, 0, st>>>(a, *batch);
       break;
     case 13:
       phase3_kernel<WPR, TH, H, 0, true><<<ntiles, T::NT, 0, st>>>(a, *batch);
