@@ -608,16 +608,29 @@ def measure_other_configs(sw, torch, stream, flush):
             "bytes_per_site": POTTS_BYTES_PER_TILE / (TW * TH), "achieved_gbs": gbs,
             "frac_of_hbm": gbs / peak_gbs, "peak": f"{peak_gbs:.0f} GB/s ({peak_kind})"}
     # O(4) phi^4 multicluster updates at the paper's kappa = 0.304 (§5's
-    # second table: L = 16..28, 10^4 updates)
+    # second table: L = 16..28, 10^4 updates), and L = 64 (16.8 M sites,
+    # 0.5 GB of field) where the update's arrays no longer fit in L2.
+    # Algorithmic bytes per site of one update: project (field 32 in,
+    # projection 8 and parent 4 out), bonds (projection 8 in, bond bits 1
+    # out), unite (bond bits 1 in; the parent walks are data dependent and
+    # not counted), roots (parent 4 in and 4 out), reflect (parent 4, flip 1,
+    # projection 8 in; the field of the half of the sites that flip, 32 in
+    # and 32 out), observables (field 32 in).
+    phi4_bytes = (32 + 8 + 4) + (8 + 1) + 1 + (4 + 4) + (4 + 1 + 8 + 0.5 * 64) + 32
     out["phi4_kappa0.304"] = {}
-    for Lp in (16, 28):
+    for Lp in (16, 28, 64):
         with sw.Phi4(Lp, 0.304, 6, stream=stream.cuda_stream) as f4:
             f4.sweep(5)
             n4 = 200
             ms4 = timed_sweeps(torch, stream, lambda: f4.sweep(n4), n4)
             f4.observables(5, n4)
+        gbs = phi4_bytes * Lp**4 / (ms4 / n4 / 1e3) / 1e9
         out["phi4_kappa0.304"][f"L{Lp}"] = {"ms_per_update": ms4 / n4, "site_updates_s": Lp**4 * n4 / (ms4 / 1e3),
-                                            "updates": n4, "minutes_per_1e4_updates": ms4 / n4 * 1e4 / 6e4}
+                                            "updates": n4, "minutes_per_1e4_updates": ms4 / n4 * 1e4 / 6e4,
+                                            "bytes_per_site": phi4_bytes, "achieved_gbs": gbs,
+                                            "frac_of_hbm": gbs / peak_gbs,
+                                            "peak": f"{peak_gbs:.0f} GB/s ({peak_kind})",
+                                            "l2": "fits in L2" if 46 * Lp**4 < 100e6 else "exceeds L2"}
     return out
 
 

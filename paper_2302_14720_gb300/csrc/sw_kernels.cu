@@ -1934,15 +1934,21 @@ __global__ void init_kernel(int8_t* spins, long long n, KeySchedule ks, int cold
 // Every spin must be +1 (0x01) or -1 (0xFF). 16 bytes per thread step,
 // four at a time with byte-wise compares; the buffer is the library's own
 // (16-byte aligned), the ragged tail goes byte by byte.
+// Every byte must be +1 or -1. A streaming read: each thread keeps four
+// independent 16-byte loads in flight per trip, so that a grid of whole SMs
+// reaches the HBM rate.
 __global__ void check_spins_kernel(const int8_t* spins, long long n, int* err) {
   const long long stride = (long long)gridDim.x * blockDim.x, i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nv = n / 16;
   const uint4* p = reinterpret_cast<const uint4*>(spins);
   auto ok4 = [](uint32_t w) { return (__vcmpeq4(w, 0x01010101u) | __vcmpeq4(w, 0xFFFFFFFFu)) == 0xFFFFFFFFu; };
   bool bad = false;
-  for (long long i = i0; i < nv; i += stride) {
-    const uint4 v = p[i];
-    bad |= !(ok4(v.x) && ok4(v.y) && ok4(v.z) && ok4(v.w));
+  for (long long i = i0; i < nv; i += 4 * stride) {
+    uint4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = i + k * stride < nv ? p[i + k * stride] : make_uint4(~0u, ~0u, ~0u, ~0u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bad |= !(ok4(v[k].x) && ok4(v[k].y) && ok4(v[k].z) && ok4(v[k].w));
   }
   for (long long i = 16 * nv + i0; i < n; i += stride) bad |= spins[i] != 1 && spins[i] != -1;
   if (bad) atomicCAS(err, 0, kErrBadSpin);
@@ -2057,7 +2063,7 @@ cudaError_t launch_init(int8_t* spins, int L, uint64_t seed, int cold, cudaStrea
 }
 
 cudaError_t launch_check_spins(const int8_t* spins, int64_t n, int* err, cudaStream_t st) {
-  check_spins_kernel<<<grid_for(n, 256), 256, 0, st>>>(spins, n, err);
+  check_spins_kernel<<<grid_for(n, 256 * 4) < 152 * 8 ? grid_for(n, 256 * 4) : 152 * 8, 256, 0, st>>>(spins, n, err);
   return cudaGetLastError();
 }
 

@@ -41,11 +41,12 @@ def test_phi4_chain_parity(sw, L, kappa, cold):
         assert np.abs(M - wM).max() <= 1e-12 * scale
 
 
-@pytest.mark.parametrize("L", [16, 28])
-def test_phi4_bench_configuration(sw, L):
+@pytest.mark.parametrize("L,n", [(16, 5), (28, 5), (64, 1)])
+def test_phi4_bench_configuration(sw, L, n):
     """The benchmark's runs (kappa = 0.304, hot start, seed 6) at the
-    smallest and largest L of the paper's table, five updates."""
-    seed, n = 6, 5
+    smallest and largest L of the paper's table, five updates, and its
+    L = 64 run (a field larger than L2), one update."""
+    seed = 6
     with sw.Phi4(L, KAPPA, seed) as f:
         f.sweep(n)
         want, wE, wM = oracle.phi4_run(L, KAPPA, seed, n)
