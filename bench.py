@@ -59,11 +59,10 @@ RW = (TW // 32) * TH  # 32-site row-words per tile
 # the stored layout (bit masks, 16-bit tile roots, border tables); slot nodes
 # (8 bytes per border component) are data dependent and not counted.
 PHASE_BYTES_PER_TILE = {
-    # spins + halo and the bond draws (two 32-bit masks per row word, drawn
-    # during the previous sweep's merge) in; spin/east/south masks, 16-bit
-    # tile roots, border-root and root masks, border slots, tile bits, slot
-    # count out
-    0: (TW * TH + TH + TW + 8 * RW) + (3 * RW * 4 + 2 * TW * TH + 2 * 4 * RW + 2 * NB + 4 * BBW + 4),
+    # spins + halo in; spin/east/south masks, 16-bit tile roots, border-root
+    # and root masks, border slots, tile bits, slot count out (a one-sweep
+    # call: phase 1 draws its own bonds)
+    0: (TW * TH + TH + TW) + (3 * RW * 4 + 2 * TW * TH + 2 * 4 * RW + 2 * NB + 4 * BBW + 4),
     # spin/east masks, roots, border-root and root masks, slot count, tile
     # bits, neighbours' halo slots in; spins out
     2: (2 * RW * 4 + 2 * TW * TH + 2 * 4 * RW + 4 + 4 * BBW + 2 * (TH + TW)) + TW * TH,
@@ -73,21 +72,22 @@ PHASE_BYTES_PER_TILE = {
 # border slot its node (read in the union walks, rewritten by the resolve
 # pass); the slot count is data dependent, so the model counts every border
 # site as a slot (an upper bound of the algorithmic bytes).
-# The next sweep's bond draws go out as well.
-PHASE_BYTES_PER_TILE[1] = 4 * BBW + 2 * (NB + TH + TW) + 4 + 3 * 8 * NB + 8 * RW
+PHASE_BYTES_PER_TILE[1] = 4 * BBW + 2 * (NB + TH + TW) + 4 + 3 * 8 * NB
 # Phase 3 of a sweep with phase 1 of the next in one launch: both kernels'
-# bytes, less the spins and halo that phase 1 then takes from shared memory.
-PHASE_BYTES_PER_TILE[4] = PHASE_BYTES_PER_TILE[0] + PHASE_BYTES_PER_TILE[2] - (TW * TH + TH + TW)
+# bytes, less the spins and halo that phase 1 then takes from shared memory,
+# plus the bond draws (two 32-bit masks per row word) that the merge phases
+# before it drew (in such calls the merge phases write them: 8 bytes per row
+# word more than PHASE_BYTES_PER_TILE[1]).
+PHASE_BYTES_PER_TILE[4] = PHASE_BYTES_PER_TILE[0] + PHASE_BYTES_PER_TILE[2] - (TW * TH + TH + TW) + 8 * RW
 PHASE_NAMES = {0: "phase1_bonds_tile_ccl", 1: "phase2_merge_resolve", 2: "phase3_flip_em", 3: "phase4_hist",
                4: "phase3_with_next_phase1"}
 SWEEP_MODEL_BYTES_PER_SITE = 10  # read spins, write+read int32 labels, write spins
 # q-state Potts sweep (§6) on the same tiles: phase 1 and phase 2 + resolve
-# as for Ising (the state bytes take the place of the spins; phase 1 draws
-# its own bonds); phase 3 reads
+# as for Ising (the state bytes take the place of the spins); phase 3 reads
 # the 16-bit tile roots, border-root and root masks, slot count, the tile's
 # slot states and the halo's slots and slot states, and writes the states.
 MS = 2 * (TW + TH)
-POTTS_BYTES_PER_TILE = (PHASE_BYTES_PER_TILE[0] - 8 * RW + PHASE_BYTES_PER_TILE[1] - 8 * RW
+POTTS_BYTES_PER_TILE = (PHASE_BYTES_PER_TILE[0] + PHASE_BYTES_PER_TILE[1]
                         + 2 * TW * TH + 2 * 4 * RW + 4 + MS + 3 * (TH + TW) + TW * TH)
 
 
