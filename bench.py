@@ -525,6 +525,29 @@ def timed_sweeps(torch, stream, fn, n: int) -> float:
     return e0.elapsed_time(e1)
 
 
+def l2_copy_gbs(torch, stream) -> float:
+    """Copy bandwidth (read + write bytes per second) between two 24 MiB
+    device buffers that stay in L2: 40 copies back and forth replayed from
+    one CUDA graph (no launch gaps), best of 5 replays."""
+    a = torch.empty(24 << 20, dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    a.fill_(1)
+    b.copy_(a)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for k in range(40):
+            (b.copy_(a) if k % 2 == 0 else a.copy_(b))
+    best = 0.0
+    with torch.cuda.stream(stream):
+        g.replay()
+        for _ in range(5):
+            ms = timed_sweeps(torch, stream, g.replay, 40)
+            best = max(best, 2 * (24 << 20) * 40 / (ms / 1e3) / 1e9)
+    del g
+    return best
+
+
 def measure_other_configs(sw, torch, stream, flush):
     """The smaller configurations and the second temperature of the headline
     lattice: per-sweep latency at L=64, the L2-resident rate with per-sweep
@@ -556,9 +579,27 @@ def measure_other_configs(sw, torch, stream, flush):
         assert (h[:, 1] > 0).all()
         lat.histogram(False)
         ms_nh = timed_sweeps(torch, stream, lambda: lat.sweep(n), n)
+    # The L=1024 state and its tables (about 9 MB) stay in L2, so its rate is
+    # set against the L2 copy bandwidth measured here (two 24 MiB buffers,
+    # L2-resident, copied back and forth), not against HBM. Algorithmic bytes
+    # per site: with statistics the one-sweep phases (phase 4's O(clusters)
+    # not counted); without, the merge phases (with their bond draws) and the
+    # fused launch of a multi-sweep call.
+    l2_gbs = l2_copy_gbs(torch, stream)
+    tiles = (1024 // TW) * (1024 // TH)
+    by_hist = (PHASE_BYTES_PER_TILE[0] + PHASE_BYTES_PER_TILE[1] + PHASE_BYTES_PER_TILE[2]) * tiles
+    by_fused = (PHASE_BYTES_PER_TILE[1] + 8 * RW + PHASE_BYTES_PER_TILE[4]) * tiles
+    g_hist = by_hist / (ms / n / 1e3) / 1e9
+    g_fused = by_fused / (ms_nh / n / 1e3) / 1e9
     out["L1024_betac_cold_hist"] = {"su_s": 1024 * 1024 * n / (ms / 1e3), "us_per_sweep": 1e3 * ms / n,
                                     "su_s_without_hist": 1024 * 1024 * n / (ms_nh / 1e3), "sweeps": n,
-                                    "l2": "state L2-resident (1 MiB spins), no flush"}
+                                    "l2": "state L2-resident (1 MiB spins), no flush",
+                                    "l2_roofline": {"peak": l2_gbs, "unit": "GB/s",
+                                                    "peak_kind": "measured live: L2-resident copy, 2 x 24 MiB",
+                                                    "bytes_per_site_hist": by_hist / 1024**2,
+                                                    "achieved_hist": g_hist, "frac_hist": g_hist / l2_gbs,
+                                                    "bytes_per_site_no_hist": by_fused / 1024**2,
+                                                    "achieved_no_hist": g_fused, "frac_no_hist": g_fused / l2_gbs}}
     # L=8192, beta=0.50, hot start seed 3, L2 flushed between sweeps
     with sw.Lattice(L, 0.50, SEED, stream=stream.cuda_stream) as lat:
         for k in range(3):

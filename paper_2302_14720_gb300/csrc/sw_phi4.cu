@@ -88,9 +88,62 @@ __device__ __forceinline__ double proj(const F4 f, const Dir& d) {
   return __fma_rn(f.w, d.r[3], __fma_rn(f.z, d.r[2], __fma_rn(f.y, d.r[1], __dmul_rn(f.x, d.r[0]))));
 }
 
-__device__ __forceinline__ int64_t nb(int64_t x, int mu, int L, int64_t stride) {
-  const int64_t c = (x / stride) % L;
-  return c == L - 1 ? x - (int64_t)(L - 1) * stride : x + stride;
+// The coordinates of site x = c0 + L c1 + L^2 c2 + L^3 c3 (O2); L^4 < 2^31,
+// so 32-bit arithmetic holds every index.
+struct Coords {
+  uint32_t c[4];
+};
+__device__ __forceinline__ Coords coords_of(uint32_t x, uint32_t L) {
+  Coords k;
+#pragma unroll
+  for (int mu = 0; mu < 3; ++mu) {
+    const uint32_t q = x / L;
+    k.c[mu] = x - q * L;
+    x = q;
+  }
+  k.c[3] = x;
+  return k;
+}
+
+// The forward neighbour of x in direction mu (periodic), stride = L^mu.
+__device__ __forceinline__ uint32_t nb(uint32_t x, int mu, const Coords& k, uint32_t L, uint32_t stride) {
+  return k.c[mu] == L - 1 ? x - (L - 1) * stride : x + stride;
+}
+
+// The bond decision of Eq. 2 for the edge (x, y): bonded iff q = a_x a_y > 0
+// and w < (1 - e^{-z}) 2^32 with z = k4 q, all in binary64 with exp_neg.
+// GB300 runs binary64 at a small fraction of its binary32 rate, so a
+// binary32 estimate decides first, from the projections rounded to binary32
+// (af, each within 2^-24 relative): with both |af| >= 2^-60 the binary64
+// product is positive exactly when the signs agree, z in binary32 (three
+// roundings of 2^-24 and two products) is within 5 * 2^-24 relative, so
+// e^{-z} from expf (2 ulp) is within 40 * 5 * 2^-24 + 2^-22 of the binary64
+// value for z <= 40, and (1 - e) 2^32 is then within 2^16 of the binary64
+// threshold. A word more than 2^18 from the estimate takes the same decision
+// as the binary64 test; the others (about 1e-4 of the edges), edges with a
+// tiny projection and z near 40 take the binary64 test itself.
+__device__ __forceinline__ bool bonded_exact(double ax, double ay, double k4, uint32_t w) {
+  const double q = __dmul_rn(ax, ay);
+  if (!(q > 0.0)) return false;
+  const double e = exp_neg(__dmul_rn(k4, q));
+  return __uint2double_rn(w) < __dmul_rn(__dsub_rn(1.0, e), 0x1p32);
+}
+
+__device__ __forceinline__ bool bonded(const double* a, uint32_t x, uint32_t y, float fx, float fy, float k4f,
+                                       double k4, uint32_t w) {
+  const float mx = fabsf(fx), my = fabsf(fy);
+  if (mx >= 0x1p-60f && my >= 0x1p-60f) {
+    if (signbit(fx) != signbit(fy)) return false;
+    const float zf = __fmul_rn(__fmul_rn(k4f, mx), my);
+    if (zf > 40.01f) return true;  // z > 40: e^{-z} is 0 in exp_neg, the threshold 2^32
+    if (zf < 39.99f) {
+      const float tf = __fmul_rn(__fsub_rn(1.0f, expf(-zf)), 0x1p32f);
+      const float wf = (float)w;  // within 2^8 of w
+      if (wf < tf - 0x1p18f) return true;
+      if (wf > tf + 0x1p18f) return false;
+    }
+  }
+  return bonded_exact(a[x], a[y], k4, w);
 }
 
 __device__ __forceinline__ double unit_interval(uint32_t w) {
@@ -143,42 +196,48 @@ __global__ void phi4_init_kernel(F4* phi, int64_t n, sw::KeySchedule ks, int col
   }
 }
 
-__global__ void phi4_project_kernel(const F4* phi, double* a, int* par, int64_t n, Dir d) {
+// The projections in binary64 and, for the bond kernel's first test, rounded
+// to binary32.
+__global__ void phi4_project_kernel(const F4* phi, double* a, float* af, int* par, int64_t n, Dir d) {
   GRID_LOOP(x, n) {
-    a[x] = proj(phi[x], d);
+    const double v = proj(phi[x], d);
+    a[x] = v;
+    af[x] = __double2float_rn(v);
     par[x] = (int)x;
   }
 }
 
-__global__ void phi4_bonds_kernel(const double* a, uint8_t* bonds, int L, int64_t n, double k4, uint32_t t,
-                                  sw::KeySchedule ks) {
-  GRID_LOOP(x, n) {
-    const uint4 w4 = sw::philox4x32_10(make_uint4((uint32_t)x, t, 4u, 0u), ks);
+__global__ void phi4_bonds_kernel(const double* a, const float* af, uint8_t* bonds, int L, int64_t n, double k4,
+                                  uint32_t t, sw::KeySchedule ks) {
+  const float k4f = __double2float_rn(k4);
+  GRID_LOOP(i, n) {
+    const uint32_t x = (uint32_t)i;
+    const Coords k = coords_of(x, (uint32_t)L);
+    const uint4 w4 = sw::philox4x32_10(make_uint4(x, t, 4u, 0u), ks);
     const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
-    const double ax = a[x];
+    const float fx = af[x];
     uint8_t b = 0;
-    int64_t stride = 1;
+    uint32_t stride = 1;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-      const double q = __dmul_rn(ax, a[nb(x, mu, L, stride)]);
-      if (q > 0.0) {
-        const double e = exp_neg(__dmul_rn(k4, q));
-        if (__uint2double_rn(w[mu]) < __dmul_rn(__dsub_rn(1.0, e), 0x1p32)) b |= (uint8_t)(1u << mu);
-      }
-      stride *= L;
+      const uint32_t y = nb(x, mu, k, (uint32_t)L, stride);
+      if (bonded(a, x, y, fx, af[y], k4f, k4, w[mu])) b |= (uint8_t)(1u << mu);
+      stride *= (uint32_t)L;
     }
     bonds[x] = b;
   }
 }
 
 __global__ void phi4_unite_kernel(const uint8_t* bonds, int* par, int L, int64_t n, int* err) {
-  GRID_LOOP(x, n) {
+  GRID_LOOP(i, n) {
+    const uint32_t x = (uint32_t)i;
     const uint8_t b = bonds[x];
     if (!b) continue;
-    int64_t stride = 1;
+    const Coords k = coords_of(x, (uint32_t)L);
+    uint32_t stride = 1;
     for (int mu = 0; mu < 4; ++mu) {
-      if ((b >> mu) & 1u) unite(par, (int)x, (int)nb(x, mu, L, stride), err);
-      stride *= L;
+      if ((b >> mu) & 1u) unite(par, (int)x, (int)nb(x, mu, k, (uint32_t)L, stride), err);
+      stride *= (uint32_t)L;
     }
   }
 }
@@ -215,13 +274,15 @@ __global__ void phi4_reflect_kernel(F4* phi, const double* a, const int* par, co
 
 __global__ void phi4_observe_kernel(const F4* phi, int L, int64_t n, double* out /* E, M0..M3 */) {
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  GRID_LOOP(x, n) {
+  GRID_LOOP(i, n) {
+    const uint32_t x = (uint32_t)i;
+    const Coords k = coords_of(x, (uint32_t)L);
     const F4 f = phi[x];
-    int64_t stride = 1;
+    uint32_t stride = 1;
     for (int mu = 0; mu < 4; ++mu) {
-      const F4 g = phi[nb(x, mu, L, stride)];
+      const F4 g = phi[nb(x, mu, k, (uint32_t)L, stride)];
       v[0] += f.x * g.x + f.y * g.y + f.z * g.z + f.w * g.w;
-      stride *= L;
+      stride *= (uint32_t)L;
     }
     v[1] += f.x;
     v[2] += f.y;
@@ -270,6 +331,7 @@ struct sw_phi4 {
   bool own_stream = false;
   F4* phi = nullptr;
   double* a = nullptr;
+  float* af = nullptr;  // the projections rounded to binary32 (the bond kernel's first test)
   int* par = nullptr;
   uint8_t* bonds = nullptr;
   uint8_t* flip = nullptr;
@@ -289,7 +351,7 @@ namespace {
   } while (0)
 
 void free_phi4(sw_phi4* h) {
-  void* ptrs[] = {h->phi, h->a, h->par, h->bonds, h->flip, h->obs, h->err};
+  void* ptrs[] = {h->phi, h->a, h->af, h->par, h->bonds, h->flip, h->obs, h->err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -346,8 +408,9 @@ int direction(uint64_t seed, uint32_t t, double r[4]) {
 int clusters(sw_phi4* h, Dir& d) {
   if (direction(h->seed, (uint32_t)h->t, d.r) != 0) return ffail(SW_EDEVICE, "no direction found");
   const int g = grid_of(h->n);
-  phi4_project_kernel<<<g, 256, 0, h->stream>>>(h->phi, h->a, h->par, h->n, d);
-  phi4_bonds_kernel<<<g, 256, 0, h->stream>>>(h->a, h->bonds, h->L, h->n, 4.0 * h->kappa, (uint32_t)h->t, h->ks);
+  phi4_project_kernel<<<g, 256, 0, h->stream>>>(h->phi, h->a, h->af, h->par, h->n, d);
+  phi4_bonds_kernel<<<g, 256, 0, h->stream>>>(h->a, h->af, h->bonds, h->L, h->n, 4.0 * h->kappa, (uint32_t)h->t,
+                                              h->ks);
   phi4_unite_kernel<<<g, 256, 0, h->stream>>>(h->bonds, h->par, h->L, h->n, h->err);
   phi4_roots_kernel<<<g, 256, 0, h->stream>>>(h->par, h->flip, h->n, (uint32_t)h->t, h->ks, h->err);
   F_CUDA(cudaGetLastError(), "phi4 update launch");
@@ -392,6 +455,7 @@ int sw_phi4_create(int32_t L, double kappa, uint64_t seed, int32_t init, void* s
   }
   if (e == cudaSuccess) e = cudaMalloc(&h->phi, n * sizeof(F4));
   if (e == cudaSuccess) e = cudaMalloc(&h->a, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->af, n * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&h->par, n * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->bonds, n);
   if (e == cudaSuccess) e = cudaMalloc(&h->flip, n);
