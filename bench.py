@@ -58,27 +58,39 @@ RW = (TW // 32) * TH  # 32-site row-words per tile
 # Algorithmic bytes per full tile: what each kernel must read and write for
 # the stored layout (bit masks, 16-bit tile roots, border tables); slot nodes
 # (8 bytes per border component) are data dependent and not counted.
-PHASE_BYTES_PER_TILE = {
-    # spins + halo in; spin/east/south masks, 16-bit tile roots, border-root
-    # and root masks, border slots, tile bits, slot count out (a one-sweep
-    # call: phase 1 draws its own bonds)
-    0: (TW * TH + TH + TW) + (3 * RW * 4 + 2 * TW * TH + 2 * 4 * RW + 2 * NB + 4 * BBW + 4),
-    # spin/east masks, roots, border-root and root masks, slot count, tile
-    # bits, neighbours' halo slots in; spins out
-    2: (2 * RW * 4 + 2 * TW * TH + 2 * 4 * RW + 4 + 4 * BBW + 2 * (TH + TW)) + TW * TH,
-}
-# Phase 2 + resolve touch O(tile perimeter): the tile's border bits and the
-# border slots of the tile and of its east and south neighbours, and per
-# border slot its node (read in the union walks, rewritten by the resolve
-# pass); the slot count is data dependent, so the model counts every border
-# site as a slot (an upper bound of the algorithmic bytes).
-PHASE_BYTES_PER_TILE[1] = 4 * BBW + 2 * (NB + TH + TW) + 4 + 3 * 8 * NB
-# Phase 3 of a sweep with phase 1 of the next in one launch: both kernels'
-# bytes, less the spins and halo that phase 1 then takes from shared memory,
-# plus the bond draws (two 32-bit masks per row word) that the merge phases
-# before it drew (in such calls the merge phases write them: 8 bytes per row
-# word more than PHASE_BYTES_PER_TILE[1]).
-PHASE_BYTES_PER_TILE[4] = PHASE_BYTES_PER_TILE[0] + PHASE_BYTES_PER_TILE[2] - (TW * TH + TH + TW) + 8 * RW
+def phase_bytes_per_tile(tw: int, th: int) -> dict:
+    """Algorithmic bytes of each kernel for one full tile of tw x th sites:
+    what it must read and write for the stored layout (bit masks, 16-bit
+    tile roots, border-root and root masks, border tables); slot nodes (8
+    bytes per border component) are data dependent and not counted."""
+    nb = 2 * th + 2 * tw                    # border sites
+    bbw = 2 * (th // 32) + 2 * (tw // 32)   # border bit words
+    rw = (tw // 32) * th                    # 32-site row words
+    d = {
+        # spins + halo in; spin/east/south masks, 16-bit tile roots,
+        # border-root and root masks, border slots, tile bits, slot count out
+        # (a one-sweep call: phase 1 draws its own bonds)
+        0: (tw * th + th + tw) + (3 * rw * 4 + 2 * tw * th + 2 * 4 * rw + 2 * nb + 4 * bbw + 4),
+        # spin/east masks, roots, border-root and root masks, slot count,
+        # tile bits, neighbours' halo slots in; spins out
+        2: (2 * rw * 4 + 2 * tw * th + 2 * 4 * rw + 4 + 4 * bbw + 2 * (th + tw)) + tw * th,
+    }
+    # Phase 2 + resolve touch O(tile perimeter): the tile's border bits and
+    # the border slots of the tile and of its east and south neighbours, and
+    # per border slot its node (read in the union walks, rewritten by the
+    # resolve pass); the slot count is data dependent, so the model counts
+    # every border site as a slot (an upper bound of the algorithmic bytes).
+    d[1] = 4 * bbw + 2 * (nb + th + tw) + 4 + 3 * 8 * nb
+    # Phase 3 of a sweep with phase 1 of the next in one launch: both
+    # kernels' bytes, less the spins and halo that phase 1 then takes from
+    # shared memory, plus the bond draws (two 32-bit masks per row word) that
+    # the merge phases before it drew (in such calls the merge phases write
+    # them: 8 bytes per row word more than d[1]).
+    d[4] = d[0] + d[2] - (tw * th + th + tw) + 8 * rw
+    return d
+
+
+PHASE_BYTES_PER_TILE = phase_bytes_per_tile(TW, TH)
 PHASE_NAMES = {0: "phase1_bonds_tile_ccl", 1: "phase2_merge_resolve", 2: "phase3_flip_em", 3: "phase4_hist",
                4: "phase3_with_next_phase1"}
 SWEEP_MODEL_BYTES_PER_SITE = 10  # read spins, write+read int32 labels, write spins
@@ -571,6 +583,7 @@ def measure_other_configs(sw, torch, stream, flush):
                         "how": "sw_sweep(1000) launches; and a one-replica batch replaying a 100-sweep graph"}
     # L=1024, beta_c, cold start seed 2, histogram every sweep (L2-resident)
     with sw.Lattice(1024, BETA, 2, sw.SW_INIT_COLD, stream=stream.cuda_stream) as lat:
+        shape1024 = sw.sw_lattice_shape(lat.h)
         lat.histogram(True)
         lat.sweep(20)
         n = 1000
@@ -586,14 +599,20 @@ def measure_other_configs(sw, torch, stream, flush):
     # not counted); without, the merge phases (with their bond draws) and the
     # fused launch of a multi-sweep call.
     l2_gbs = l2_copy_gbs(torch, stream)
-    tiles = (1024 // TW) * (1024 // TH)
-    by_hist = (PHASE_BYTES_PER_TILE[0] + PHASE_BYTES_PER_TILE[1] + PHASE_BYTES_PER_TILE[2]) * tiles
-    by_fused = (PHASE_BYTES_PER_TILE[1] + 8 * RW + PHASE_BYTES_PER_TILE[4]) * tiles
+    info = sw.sw_shape_info(shape1024)
+    tw1, th1 = info["tile_w"], info["tile_h"]
+    pb = phase_bytes_per_tile(tw1, th1)
+    tiles = (1024 // tw1) * (1024 // th1)
+    by_hist = (pb[0] + pb[1] + pb[2]) * tiles
+    # without statistics: the fused launch where the shape has it, else the
+    # one-sweep phases
+    by_fused = ((pb[1] + 8 * (tw1 // 32) * th1 + pb[4]) if shape1024 in (4, 6) else (pb[0] + pb[1] + pb[2])) * tiles
     g_hist = by_hist / (ms / n / 1e3) / 1e9
     g_fused = by_fused / (ms_nh / n / 1e3) / 1e9
     out["L1024_betac_cold_hist"] = {"su_s": 1024 * 1024 * n / (ms / 1e3), "us_per_sweep": 1e3 * ms / n,
                                     "su_s_without_hist": 1024 * 1024 * n / (ms_nh / 1e3), "sweeps": n,
                                     "l2": "state L2-resident (1 MiB spins), no flush",
+                                    "tile": f"{tw1}x{th1}",
                                     "l2_roofline": {"peak": l2_gbs, "unit": "GB/s",
                                                     "peak_kind": "measured live: L2-resident copy, 2 x 24 MiB",
                                                     "bytes_per_site_hist": by_hist / 1024**2,

@@ -481,8 +481,14 @@ int sw_shape_info(int32_t shape, int32_t* tile_w, int32_t* tile_h, int32_t* stri
 /* Process-wide preference: lattices whose side L has ceil(log2 L) ==
  * log2_bucket (0..16) use `shape` from now on in sw_create, and batches
  * created with shape -1 use the entry of their largest L; shape -1 restores
- * the built-in default. Results never depend on the shape. */
+ * the built-in default (64x64 tiles up to L = 64; then for a lattice 128x32
+ * tiles up to L = 1024 and 128x64 above, for a batch 128x64). Results never
+ * depend on the shape. */
 int sw_tune_shape(int32_t log2_bucket, int32_t shape);
+
+/* The tile shape index a lattice was created with (its tiled path; sides up
+ * to 144 run whole sweeps in one CTA unless SW_TILE_SHAPE is set). */
+int sw_lattice_shape(sw_lattice* h, int32_t* shape);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* sw_last_error(void);

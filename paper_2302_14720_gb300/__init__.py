@@ -79,6 +79,7 @@ SIGNATURES = {
     "sw_num_shapes": (ctypes.c_int, []),
     "sw_shape_info": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P]),
     "sw_tune_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
+    "sw_lattice_shape": (ctypes.c_int, [ctypes.c_void_p, _P]),
     "sw_last_error": (ctypes.c_char_p, []),
     "sw_potts_threshold": (ctypes.c_uint32, [ctypes.c_double]),
     "sw_potts_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64,
@@ -275,6 +276,12 @@ def sw_shape_info(shape: int) -> dict:
 
 def sw_tune_shape(log2_bucket: int, shape: int) -> None:
     _check(_lib.sw_tune_shape(int(log2_bucket), int(shape)), "sw_tune_shape")
+
+
+def sw_lattice_shape(h: int) -> int:
+    v = np.zeros(1, np.int32)
+    _check(_lib.sw_lattice_shape(h, _host_ptr(v)), "sw_lattice_shape")
+    return int(v[0])
 
 
 def sw_last_error() -> str:

@@ -63,7 +63,9 @@ int bucket_of(int L) {
   return b < kBuckets ? b : kBuckets - 1;
 }
 
-int shape_for(int L) {
+// lattice: the shape of a lone lattice (sw_create); else of a batch whose
+// largest side is L.
+int shape_for(int L, bool lattice) {
   if (const char* env = getenv("SW_TILE_SHAPE")) {
     const int v = atoi(env);
     if (v >= 0 && v < sw::kNumShapes) return v;
@@ -73,13 +75,19 @@ int shape_for(int L) {
   });
   const int t = g_tuned[bucket_of(L)].load();
   if (t >= 0) return t;
-  return L <= 64 ? 2 : 6;
+  if (L <= 64) return 2;
+  // A lone lattice of side <= 1024 has at most 128 tiles of 128 x 64, less
+  // than one wave of 152 SMs; with 128 x 32 tiles twice as many CTAs share
+  // each phase's latency (measured on GB300 at L = 256 .. 1024: one-sweep
+  // calls 12 %, sweeps with statistics 9 % faster, chains even). Batches keep
+  // 128 x 64, whose fused schedule the 128 x 32 shape does not have.
+  return lattice && L <= 1024 ? 7 : 6;
 }
 
 }  // namespace
 
 namespace sw {
-int default_shape(int L) { return shape_for(L); }
+int default_shape(int L) { return shape_for(L, false); }
 }  // namespace sw
 
 namespace sw {
@@ -310,7 +318,7 @@ int sw_create(int32_t L, double beta, uint64_t seed, int32_t init, void* stream,
   h->beta = beta;
   h->seed = seed;
   h->thr = threshold_of(beta);
-  h->shape = shape_for(L);
+  h->shape = shape_for(L, true);
   h->tiles_only = getenv("SW_TILE_SHAPE") != nullptr;
   h->ks = sw::make_key_schedule(seed);
   cudaGetDevice(&h->device);
@@ -605,8 +613,14 @@ int sw_shape_info(int32_t shape, int32_t* tile_w, int32_t* tile_h, int32_t* stri
 int sw_tune_shape(int32_t log2_bucket, int32_t shape) {
   if (log2_bucket < 0 || log2_bucket >= kBuckets) return fail(SW_EINVAL, "bucket must be in [0, %d)", kBuckets);
   if (shape < -1 || shape >= sw::kNumShapes) return fail(SW_EINVAL, "unknown tile shape %d", shape);
-  shape_for(2);  // initialise the table
+  shape_for(2, true);  // initialise the table
   g_tuned[log2_bucket].store(shape);
+  return SW_OK;
+}
+
+int sw_lattice_shape(sw_lattice* h, int32_t* shape) {
+  if (!h || !shape) return fail(SW_EINVAL, "NULL argument");
+  *shape = h->shape;
   return SW_OK;
 }
 

@@ -308,3 +308,16 @@ def test_set_state_rejects_every_invalid_spin(sw, L, where, value):
             lat.set_state(s, 0)
         assert ei.value.status == sw.SW_EINVAL
         assert lat.t == 1
+
+
+def test_default_tile_shapes(sw):
+    # built-in defaults (no tuning installed, SW_TILE_SHAPE unset): a lone
+    # lattice takes 128x32 tiles up to L = 1024 and 128x64 above; a batch
+    # keeps 128x64 (results never depend on the shape; the parity tests
+    # above run every shape)
+    assert "SW_TILE_SHAPE" not in os.environ
+    for L, want in ((200, 7), (1024, 7), (1025, 6), (4096, 6)):
+        with sw.Lattice(L, BETA_C, 1, sw.SW_INIT_HOT) as lat:
+            got = sw.sw_lattice_shape(lat.h)
+        assert got == want, (L, got)
+        assert sw.sw_shape_info(got)["tile_w"] == 128
