@@ -133,7 +133,7 @@ __device__ __forceinline__ bool bonded(const double* a, uint32_t x, uint32_t y, 
                                        double k4, uint32_t w) {
   const float mx = fabsf(fx), my = fabsf(fy);
   if (mx >= 0x1p-60f && my >= 0x1p-60f) {
-    if (signbit(fx) != signbit(fy)) return false;
+    if ((__float_as_uint(fx) ^ __float_as_uint(fy)) >> 31) return false;  // opposite signs: q < 0
     const float zf = __fmul_rn(__fmul_rn(k4f, mx), my);
     if (zf > 40.01f) return true;  // z > 40: e^{-z} is 0 in exp_neg, the threshold 2^32
     if (zf < 39.99f) {
