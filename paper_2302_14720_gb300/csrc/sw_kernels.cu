@@ -1220,12 +1220,18 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, uint3
   // the tile roots (every tile's block is 16-byte aligned) travel on the
   // copy engine while the decisions are drawn; the first parent read waits
   if (tid == 0) bulk_load_start(par, groots, TW * TH * sizeof(uint16_t), &s_roots_bar);
-  uint32_t s[H], e_int[H];
+  // the global loads that only read phase 1's output go out together here
+  // (spin and east masks, border-root and root masks, the slot count), so
+  // that no later stage waits on a DRAM round trip of its own
+  const uint32_t* grb = a.tb.rbits + (size_t)P.tile * RW;
+  const int nsl = a.tb.nslots[P.tile];
+  uint32_t s[H], e_int[H], rbw[H];
 #pragma unroll
   for (int r = 0; r < H; ++r) {
     const int y = y0r + r, rw = y * WPR + w, base = y * TW + 32 * w;
     s[r] = tb[rw];
     e_int[r] = tb[RW + rw] & ~lbit;
+    rbw[r] = LABELS ? 0u : grb[rw];
     s_bmask[rw] = gbm[rw];
     if (HIST) {  // the 32 sizes of this row word: 16 words of two 16-bit counters
       int4* z = reinterpret_cast<int4*>(s_size + base / 2);
@@ -1237,7 +1243,6 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, uint3
     for (int i = tid; i < 34; i += NT) s_hist[i] = 0ull;
   for (int i = tid; i < (MS + 31) / 32; i += NT) s_slotdec[i] = 0u;
   __syncthreads();
-  const int nsl = a.tb.nslots[P.tile];
   if (block_popc_prefix<RW, NT>(s_bmask, s_pre, s_wsum) != nsl && tid == 0) atomicCAS(a.tb.err, 0, kErrSlotOverflow);
 
   // ---- this tile's slots: root key and flip, as the resolve pass left them
@@ -1305,7 +1310,6 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, uint3
       const uint32_t key = (uint32_t)(P.y0 + x / TW) * (uint32_t)L + (uint32_t)(P.x0 + x % TW);
       return decision_bit(key, a.t, a.ks, a.rule);
     };
-    const uint32_t* grb = a.tb.rbits + (size_t)P.tile * RW;
 #pragma unroll
     for (int r = 0; r < H; ++r) s_flip[(y0r + r) * WPR + w] = 0u;
     __syncwarp();
@@ -1313,7 +1317,7 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, uint3
     for (int r = 0; r < H; ++r) {
       const int y = y0r + r, base = y * TW + 32 * w, rw = y * WPR + w;
       const uint32_t bm = s_bmask[rw];
-      uint32_t inner = r < nv ? grb[rw] & ~bm : 0u;
+      uint32_t inner = r < nv ? rbw[r] & ~bm : 0u;
       uint32_t fl = 0, B = r < nv ? bm : 0u;
       while (B) {
         const int b = __ffs(B) - 1;
@@ -1484,14 +1488,13 @@ __device__ __forceinline__ bool phase3_body(P3Shared<WPR, TH, H, MODE>& S, uint3
     // and bins 0-7 (8-bit fields: at most 64 roots a thread) add up in
     // registers and once per warp into the shared histogram.
     __syncthreads();
-    const uint32_t* grb = a.tb.rbits + (size_t)P.tile * RW;
     uint32_t cnt = 0u, sq = 0u, bins03 = 0u, bins47 = 0u;
 #pragma unroll
     for (int r = 0; r < H; ++r) {
       if (r >= nv || !wmask) continue;
       const int base = (y0r + r) * TW + 32 * w, rw = (y0r + r) * WPR + w;
       const uint32_t bm = s_bmask[rw];
-      for (uint32_t m = grb[rw]; m; m &= m - 1) {
+      for (uint32_t m = rbw[r]; m; m &= m - 1) {
         const int b = __ffs(m) - 1, l = base + b;
         const uint32_t sz = (s_size[l >> 1] >> ((l & 1) << 4)) & 0xffffu;
         if ((bm >> b) & 1u) {
