@@ -133,7 +133,12 @@ int sw_destroy(sw_lattice* h);
  * synchronises. A lattice with L <= 144 and statistics off runs all n
  * sweeps in one CTA-sized launch (the whole lattice in shared memory)
  * unless the environment variable SW_TILE_SHAPE was set at sw_create, which
- * keeps it on the tiled path; the results are the same. */
+ * keeps it on the tiled path; the results are the same. Between the sweeps
+ * of one call the bond draws of the next sweep (C5: they depend on the
+ * seed, the counter and the site, not on the spins) are taken during the
+ * current sweep's cross-tile merge; a later call whose first counter is the
+ * one they were drawn for reads them too (0.25 byte per site of the
+ * handle's memory). */
 int sw_sweep(sw_lattice* h, int32_t n);
 
 /* Current sweep counter t (the counter the next sweep will use). */
