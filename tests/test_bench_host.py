@@ -90,3 +90,23 @@ def test_phase_byte_models_cover_every_sweep_kernel():
         assert bench.PHASE_BYTES_PER_TILE[p] > 0
     # phase 1 moves at least the spins in and the 16-bit labels out
     assert bench.PHASE_BYTES_PER_TILE[0] >= 3 * bench.TW * bench.TH
+
+
+def test_byte_model_per_site():
+    # the per-kernel algorithmic bytes of the 128x64 tile, per site, as the
+    # layout states them: phase 1 reads 1 B of spins (+ halo) and writes the
+    # masks (0.375 B), 16-bit labels (2 B), border-root and root masks
+    # (0.25 B) and border tables; phase 3 reads masks, labels and root masks
+    # and writes 1 B of spins
+    pb = bench.phase_bytes_per_tile(128, 64)
+    per = {k: v / (128 * 64) for k, v in pb.items()}
+    assert abs(per[0] - 3.7485) < 1e-3
+    assert abs(per[2] - 3.5532) < 1e-3
+    assert abs(per[1] - 1.2720) < 1e-3
+    # the fused launch: both, less the spins and halo handed over on chip,
+    # plus the pre-drawn bond masks (8 B per 32 sites)
+    assert pb[4] == pb[0] + pb[2] - (128 * 64 + 64 + 128) + 8 * 4 * 64
+    assert bench.PHASE_BYTES_PER_TILE == pb
+    # the border terms grow per site as the tile shrinks
+    small = bench.phase_bytes_per_tile(128, 32)
+    assert small[1] / (128 * 32) > per[1] and small[0] / (128 * 32) > per[0]
