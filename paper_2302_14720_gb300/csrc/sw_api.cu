@@ -3,6 +3,7 @@
 // of a sweep runs in the kernels of sw_kernels.cu.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -173,9 +174,25 @@ cudaError_t take_event(sw_lattice* h, cudaEvent_t* ev) {
   return cudaEventCreate(ev);
 }
 
+// An NVTX range over a scope: profilers (ncu --nvtx, nsys) see each phase
+// launch and each call under its name; without an attached tool the calls
+// are no-ops.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+const char* const kPhaseRange[SW_TIMING_PHASES] = {"sw phase 1: bonds + tile clusters",
+                                                   "sw phase 2: cross-tile merge + resolve",
+                                                   "sw phase 3: new spins + E/M",
+                                                   "sw phase 4: cluster statistics",
+                                                   "sw phase 3 + next phase 1"};
+
 // Launch one phase, bracketed by timing events when sw_timing is on.
 template <typename F>
 cudaError_t timed_phase(sw_lattice* h, int phase, F&& launch) {
+  NvtxRange range(kPhaseRange[phase]);
   if (!h->timing_on) return launch();
   sw_lattice::Mark m{phase, nullptr, nullptr};
   cudaError_t e = take_event(h, &m.start);
@@ -379,6 +396,7 @@ int sw_destroy(sw_lattice* h) {
 }
 
 int sw_sweep(sw_lattice* h, int32_t n) {
+  NvtxRange range("sw_sweep");
   if (!h) return fail(SW_EINVAL, "handle is NULL");
   if (n < 0) return fail(SW_EINVAL, "n must be >= 0");
   if (n == 0) return SW_OK;

@@ -6,6 +6,7 @@
 // is captured once per n as a CUDA graph and replayed until the power-of-two
 // bucket of the tile count or a table's capacity changes.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -378,6 +379,11 @@ int sw_batch_remove(sw_batch* b, int32_t slot) {
 }
 
 int sw_batch_sweep(sw_batch* b, int32_t n) {
+  // an NVTX range over the call for profilers (a no-op without one)
+  struct Range {
+    Range() { nvtxRangePushA("sw_batch_sweep"); }
+    ~Range() { nvtxRangePop(); }
+  } range;
   if (!b) return bfail(SW_EINVAL, "batch is NULL");
   if (n < 0) return bfail(SW_EINVAL, "n must be >= 0");
   if (n == 0) return SW_OK;
